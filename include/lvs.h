@@ -1,0 +1,260 @@
+/*
+ * lvs.h -- C ABI of the GB300 Leuvenshtein library (encrypted edit distance
+ * with one programmable bootstrap per cell).
+ *
+ * Method: "Leuvenshtein: Efficient FHE-based Edit Distance Computation with
+ * Single Bootstrap per Cell" (Legiest, D'Anvers, Spasic, Tran, Verbauwhede,
+ * arXiv 2508.14568).  Section references below are to that paper.
+ *
+ * Problem statement followed by the calls (Section 1, Section 5, Section 6):
+ * a client encrypts its strings, a server computes edit distances on the
+ * ciphertexts with its server key, and the client decrypts the result.
+ *
+ * General conventions
+ *   - Every call returns lvs_status.  Out-pointers are written only on LVS_OK.
+ *     lvs_last_error() returns a thread-local message for the last failure.
+ *   - Handles returned through out-pointers are owned by the caller and
+ *     released with the matching lvs_*_free (NULL is accepted and ignored).
+ *     Input handles are borrowed for the duration of the call.
+ *   - Host pointers are plain CPU memory; "device" pointers are CUDA global
+ *     memory of the context's device.  All integers are little-endian.
+ *   - Ciphertexts: an LWE ciphertext of dimension d is d+1 uint64 words
+ *     (mask a[0..d-1], body b), torus Z_{2^64}, plaintext Z_32 encoded as
+ *     value * 2^59 (Section 2.2: 4 message bits + 1 padding bit).  "Big"
+ *     ciphertexts have d = k*N (the GLWE key seen as an LWE key); all
+ *     transmitted and stored ciphertexts are big.
+ *   - Batch calls are asynchronous on the context's CUDA stream; calls that
+ *     return host data (lvs_decrypt, lvs_result_export) synchronise it.
+ *   - String lengths are not hidden (the paper's loops run over m and n).
+ *   - There is no CPU fallback: compute calls fail with LVS_ERR_CUDA when no
+ *     usable GPU is present.
+ */
+#ifndef LVS_H
+#define LVS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LVS_OK = 0,
+    LVS_ERR_ARG = 1,          /* invalid argument (NULL, size, alphabet, symbol) */
+    LVS_ERR_OOM = 2,          /* host or device allocation failed                */
+    LVS_ERR_CUDA = 3,         /* CUDA runtime error (message in lvs_last_error)  */
+    LVS_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up              */
+    LVS_ERR_NOISE_BUDGET = 5, /* predicted key noise exceeds the parameter budget */
+    LVS_ERR_STATE = 6         /* not ready / wrong state (e.g. poll before done) */
+} lvs_status;
+
+/* Symbol alphabets.  ASCII7: 7-bit characters split into a 4-bit and a 3-bit
+ * symbol, 2 ciphertexts per character, 2-PBS equality (Section 4.3, Algorithm
+ * alg_ascii).  27: 'A'..'Z' -> 0..25, ' ' -> 26, same 4+1-bit split and 2-PBS
+ * equality.  DNA4: A,C,G,T -> 0..3, one ciphertext per character, 1-PBS
+ * equality (Section 4.1, used for DNA in Section 6.3). */
+typedef enum { LVS_ALPHA_ASCII7 = 0, LVS_ALPHA_27 = 1, LVS_ALPHA_DNA4 = 2 } lvs_alphabet;
+
+/* TFHE parameters (Section 2.2 and Section 6.2 name only the family "4-bit
+ * message, 0-bit carry" with a padding bit; numeric values are chosen by this
+ * library).  Supported: k = 1, N in {512, 2048}, pbs_level * pbs_base_log <= 26
+ * with pbs_level in {1, 2}, ks_level * ks_base_log <= 30. */
+typedef struct lvs_params {
+    uint32_t n;               /* LWE dimension after key switching           */
+    uint32_t k;               /* GLWE dimension (1)                          */
+    uint32_t N;               /* polynomial size                             */
+    uint32_t pbs_level;       /* bootstrapping-key gadget levels             */
+    uint32_t pbs_base_log;    /* log2 of the bootstrapping gadget base       */
+    uint32_t ks_level;        /* key-switching-key gadget levels             */
+    uint32_t ks_base_log;     /* log2 of the key-switching gadget base       */
+    uint32_t lwe_noise_log2;  /* TUniform bound (log2) of key-switching noise */
+    uint32_t glwe_noise_log2; /* TUniform bound (log2) of GLWE/fresh noise   */
+} lvs_params;
+
+/* Default set for the paper's workloads: n=834, k=1, N=2048, pbs 2 x 2^13,
+ * ks 5 x 2^3, noise bounds 2^45 / 2^17. */
+void lvs_params_default(lvs_params *out);
+/* Small INSECURE set (n=64, N=512, same gadgets) for fast parity tests. */
+void lvs_params_test(lvs_params *out);
+
+typedef struct lvs_client_key lvs_client_key; /* secret keys, host only          */
+typedef struct lvs_server_key lvs_server_key; /* BSK + KSK, host copy            */
+typedef struct lvs_ctx lvs_ctx;               /* device, stream, device keys     */
+typedef struct lvs_ct_string lvs_ct_string;   /* encrypted string (host memory)  */
+typedef struct lvs_result lvs_result;         /* encrypted distances of a batch  */
+typedef struct lvs_eq_table lvs_eq_table;     /* preprocessed EQ9 table (device) */
+typedef struct lvs_server lvs_server;         /* continuous-batching server      */
+
+const char *lvs_last_error(void);
+const char *lvs_version(void);
+
+/* ---------------------------------------------------------------- keys */
+
+/* Key generation from a 64-bit seed (deterministic: the same seed gives the
+ * same keys on every machine).  Client key: binary LWE key s (n) and binary
+ * GLWE key S (k*N).  Server key: bootstrapping key BSK_i = GGSW_S(s_i) and
+ * key-switching key KSK (big key -> s).  Randomness: SplitMix64 streams,
+ * TUniform noise.  Runs on host threads. */
+lvs_status lvs_keygen(const lvs_params *params, uint64_t seed,
+                      lvs_client_key **client, lvs_server_key **server);
+void lvs_client_key_free(lvs_client_key *ck);
+void lvs_server_key_free(lvs_server_key *sk);
+
+/* Raw key material, for serialisation and tests.  Sizes in uint64 words:
+ * lwe_key n, glwe_key k*N, bsk n*(k+1)*pbs_level*(k+1)*N laid out
+ * [i][row = j*pbs_level + lev-1][component][coefficient], ksk
+ * k*N*ks_level*(n+1) laid out [u][lev-1][n+1].  dst must hold the size;
+ * pass dst = NULL to query it in *words. */
+lvs_status lvs_client_key_export(const lvs_client_key *ck, uint64_t *lwe_key, size_t *lwe_words,
+                                 uint64_t *glwe_key, size_t *glwe_words);
+lvs_status lvs_server_key_export(const lvs_server_key *sk, uint64_t *bsk, size_t *bsk_words,
+                                 uint64_t *ksk, size_t *ksk_words);
+lvs_status lvs_server_key_params(const lvs_server_key *sk, lvs_params *out);
+
+/* ---------------------------------------------------------------- context */
+
+/* Creates a device context: uploads the server key to GPU `device`, converts
+ * the bootstrapping key to the NTT domain (three 30-bit primes, in the
+ * register order of the blind-rotation kernel) and sets up tables.  `stream`
+ * is a cudaStream_t to run on (NULL = a new non-blocking stream owned by the
+ * context).  Device memory: about 1.5x the BSK plus the KSK. */
+lvs_status lvs_ctx_create(const lvs_server_key *sk, int device, void *stream, lvs_ctx **out);
+void lvs_ctx_free(lvs_ctx *ctx);
+lvs_status lvs_ctx_synchronize(lvs_ctx *ctx);
+
+/* ---------------------------------------------------------------- client */
+
+/* Encrypts s[0..len) (Section 4.3 split for ASCII7 / 27 symbols; one symbol
+ * for DNA4).  Each symbol is one fresh big LWE ciphertext whose randomness is
+ * the SplitMix64 stream (noise_seed, ENC, string_id, 2*char + symbol).
+ * Fails with LVS_ERR_ARG on a character outside the alphabet.  len may be 0. */
+lvs_status lvs_encrypt_string(const lvs_client_key *ck, const uint8_t *s, size_t len,
+                              lvs_alphabet alphabet, uint64_t noise_seed, uint64_t string_id,
+                              lvs_ct_string **out);
+void lvs_ct_string_free(lvs_ct_string *s);
+/* Number of characters / symbols per character / big dimension k*N. */
+lvs_status lvs_ct_string_info(const lvs_ct_string *s, size_t *len, uint32_t *symbols,
+                              uint32_t *big_dim, lvs_alphabet *alphabet);
+/* Ciphertexts laid out [char][symbol][k*N+1] (host). dst = NULL: size query. */
+lvs_status lvs_ct_string_export(const lvs_ct_string *s, uint64_t *dst, size_t *words);
+/* Wraps host ciphertexts (copied) as an encrypted string. */
+lvs_status lvs_ct_string_import(const uint64_t *src, size_t len, lvs_alphabet alphabet,
+                                uint32_t big_dim, lvs_ct_string **out);
+
+/* Copies the ciphertexts of s to device memory of the context's GPU and keeps
+ * them with the string (released by lvs_ct_string_free); batch calls then read
+ * the device copy instead of uploading.  Synchronous.  Calling it again is a
+ * no-op. */
+lvs_status lvs_ct_string_upload(lvs_ctx *ctx, lvs_ct_string *s);
+
+/* Decrypts one big LWE ciphertext to its Z_32 plaintext (round(phase/2^59)). */
+lvs_status lvs_decrypt_lwe(const lvs_client_key *ck, const uint64_t *ct, uint32_t *value);
+/* Encrypts one Z_32 value as a big LWE ciphertext with the stream
+ * (noise_seed, ENC, i0, i1). */
+lvs_status lvs_encrypt_lwe(const lvs_client_key *ck, uint32_t value, uint64_t noise_seed,
+                           uint64_t i0, uint64_t i1, uint64_t *ct);
+
+/* ---------------------------------------------------------------- server */
+
+/* Edit-distance options.  band < 0: exact full matrix (the configurations of
+ * this library compute every cell). */
+typedef struct lvs_opts {
+    int32_t band;          /* reserved: must be -1 (full matrix)                 */
+    int32_t use_graph;     /* 1: capture the wavefront launches in a CUDA graph  */
+    int32_t reserved[6];
+} lvs_opts;
+void lvs_opts_default(lvs_opts *o);
+
+/* Encrypted equality of characters a[i] and b[j] (Algorithm alg_ascii: 2 PBS
+ * for ASCII7 / 27 symbols; Section 4.1: 1 PBS for DNA4).  times9 != 0 gives
+ * enc(9*EQ) (Eq. eq_eqlut9), else enc(EQ).  The result holds one ciphertext. */
+lvs_status lvs_eq(lvs_ctx *ctx, const lvs_ct_string *a, size_t i, const lvs_ct_string *b,
+                  size_t j, int times9, lvs_result **out);
+
+/* Leuvenshtein edit distances of npairs encrypted pairs (a[p], b[p])
+ * (Algorithm algo_complete: per cell 2 equality PBS + 1 cell PBS with the key
+ * of Eq. eq_keyeq2; DNA4: 1 + 1).  All pairs advance together: launch s
+ * bootstraps the union over pairs of {cell PBS of anti-diagonal s-2, EQ9 of
+ * s-1, EQ1 of s} (Section 6.2 "Parallelism": cells of one anti-diagonal are
+ * independent).  The result holds, per pair, the encrypted last row
+ * h[m][1..n] and the plaintext m; the distance is m + sum_j dec(h[m][j]).
+ * Both strings of a pair must share the alphabet; lengths may be 0. */
+lvs_status lvs_edit_distance_batch(lvs_ctx *ctx, const lvs_ct_string *const *a,
+                                   const lvs_ct_string *const *b, size_t npairs,
+                                   const lvs_opts *opts, lvs_result **out);
+
+/* Preprocessing of Section 5: for the encrypted string `enc`, the table
+ * T[sigma][i] = enc(9 * EQ(a_i, sigma)) for every symbol sigma of `subset`
+ * (nsub plaintext characters of the string's alphabet; NULL = whole alphabet:
+ * 128 / 27 / 4 symbols).  Cost: nsub * len * (2 or 1) PBS.  Device memory. */
+lvs_status lvs_preprocess(lvs_ctx *ctx, const lvs_ct_string *enc, const uint8_t *subset,
+                          size_t nsub, lvs_eq_table **out);
+void lvs_eq_table_free(lvs_eq_table *t);
+
+/* Online phase of Section 5: distance of each preprocessed encrypted string
+ * t[q] to the plaintext string plain[q] (plain_len[q] characters, all in the
+ * table's subset).  EQ9[i][j] = T[b_j][i] is a device gather (0 PBS); one
+ * cell PBS per cell. */
+lvs_status lvs_edit_distance_preprocessed_batch(lvs_ctx *ctx, const lvs_eq_table *const *t,
+                                                const uint8_t *const *plain,
+                                                const size_t *plain_len, size_t n,
+                                                const lvs_opts *opts, lvs_result **out);
+
+/* Number of items in a result, and for item `pair`: m and n. */
+lvs_status lvs_result_info(const lvs_result *r, size_t *items, size_t pair, size_t *m, size_t *n);
+/* Copies the ciphertexts of item `pair` (n big LWE ciphertexts, or 1 for
+ * lvs_eq) to host memory dst ([n][k*N+1]).  dst = NULL: size query. */
+lvs_status lvs_result_export(const lvs_result *r, size_t pair, uint64_t *dst, size_t *words);
+void lvs_result_free(lvs_result *r);
+
+/* Client side: decrypts item `pair` to the edit distance m + sum_j h[m][j]
+ * (each h decoded to {-1, 0, 1}); for an lvs_eq result, the decoded value. */
+lvs_status lvs_decrypt(const lvs_client_key *ck, const lvs_result *r, size_t pair, uint32_t *dist);
+/* Decrypts every item of a result; dist has room for `items` values. */
+lvs_status lvs_decrypt_all(const lvs_client_key *ck, const lvs_result *r, uint32_t *dist);
+
+/* ---------------------------------------------------------------- low level */
+
+/* PBS on device buffers (Section 2.2; key switch -> modulus switch -> blind
+ * rotation -> sample extract).  d_in: count big ciphertexts, row stride
+ * in_stride words (>= k*N+1); d_lut: count*16 bytes, LUT values in Z_32 (a
+ * 16-entry table, inputs 16..31 give the negation, Table table_lutrelu);
+ * d_out: count big ciphertexts with row stride out_stride.  Asynchronous on
+ * the context stream; buffers must stay valid until it completes.  Scratch
+ * memory is owned by the context. */
+lvs_status lvs_pbs_batch_device(lvs_ctx *ctx, const uint64_t *d_in, size_t in_stride,
+                                const uint8_t *d_lut, uint64_t *d_out, size_t out_stride,
+                                size_t count);
+
+/* Key switch + modulus switch only: d_out receives count * (n+1) uint32
+ * values round(a * 2N / 2^64) of the key-switched ciphertexts. */
+lvs_status lvs_keyswitch_batch_device(lvs_ctx *ctx, const uint64_t *d_in, size_t in_stride,
+                                      uint32_t *d_out, size_t count);
+
+/* Exact negacyclic products mod 2^64 through the NTT/CRT path of the blind
+ * rotation: for each of count items, out = sum_{r<4} dig[r] * poly[r][c] for
+ * c in {0,1}, with dig (int32, |d| <= 4096) [count][4][N] and poly (uint64)
+ * [count][4][2][N]; out [count][2][N].  Tests the product kernel alone. */
+lvs_status lvs_poly_mul_device(lvs_ctx *ctx, const int32_t *d_dig, const uint64_t *d_poly,
+                               uint64_t *d_out, size_t count);
+
+/* Kernel timing over a region of calls (CUDA events on the context stream).
+ * kind: 0 = blind rotation kernel, 1 = key-switch kernel. */
+typedef struct lvs_kernel_stats {
+    uint64_t launches;        /* kernel launches timed                          */
+    uint64_t items;           /* PBS (or key switches) processed by them        */
+    double total_ms;          /* sum of event-measured durations                */
+} lvs_kernel_stats;
+lvs_status lvs_ctx_set_timing(lvs_ctx *ctx, int enable);
+lvs_status lvs_ctx_kernel_stats(lvs_ctx *ctx, int kind, lvs_kernel_stats *out);
+/* PBS executed by the context since creation (counter, host side). */
+lvs_status lvs_ctx_pbs_count(lvs_ctx *ctx, uint64_t *out);
+/* CUDA kernels launched by the context since creation (counter, host side;
+ * a launch inside a CUDA graph counts when the graph is launched). */
+lvs_status lvs_ctx_launch_count(lvs_ctx *ctx, uint64_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LVS_H */

@@ -1,0 +1,473 @@
+// CUDA kernels of the Leuvenshtein hot path on GB300 (sm_103a):
+//   k_keyswitch     gather of the PBS input (a linear combination of big
+//                   ciphertexts), key switch big key -> s and modulus switch
+//   k_blind_rotate  persistent blind rotation: test-polynomial (LUT) encoding,
+//                   n CMux / external products through the exact NTT path,
+//                   sample extract and the Leuvenshtein cell epilogue
+//   k_bsk_to_ntt    one-time conversion of the bootstrapping key to the NTT
+//                   domain, in the register order of k_blind_rotate
+// plus small helpers and a product-only kernel for parity tests.
+#include <algorithm>
+#include <cstdio>
+
+#include "lvs_internal.hpp"
+#include "ntt.cuh"
+
+namespace lvs {
+namespace dev {
+
+__constant__ PrimeConsts c_pc;
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ uint32_t residue_of_signed(int64_t x, uint32_t p)
+{
+    int64_t r = x % (int64_t)p;
+    return (uint32_t)(r < 0 ? r + p : r);
+}
+
+// Value of the rotated test polynomial v' = X^{-box/2} v, v[t] = f[t / box] * Delta,
+// at index idx in [0, 2N) of X^{-b} v' (negacyclic extension).
+template <int LOGN>
+__device__ __forceinline__ uint64_t test_poly_at(const uint8_t (&f)[16], uint32_t idx)
+{
+    constexpr uint32_t N = 1u << LOGN, box = N / 16;
+    const bool neg = idx >= N;
+    const uint32_t t = idx & (N - 1);
+    uint64_t v;
+    if (t < N - box / 2) v = (uint64_t)(f[(t + box / 2) / box] & 31u) << kDeltaLog;
+    else v = 0 - ((uint64_t)(f[0] & 31u) << kDeltaLog);
+    return neg ? 0 - v : v;
+}
+
+// External product core for prime group g: digit residues d (L0 layout, in
+// [0, p)) -> forward NTT -> Montgomery products with the key slice `key`
+// ([16][T][8] u32 for this prime, this thread at +tau*8) -> inverse NTT ->
+// residues of the two output polynomials written to crt[(g*2+j)*N + e].
+template <int LOGN>
+__device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][16], const uint32_t *__restrict__ key,
+                                                 uint32_t *buf, uint32_t *crt, uint32_t tau, int g,
+                                                 const uint2 *__restrict__ twf, const uint2 *__restrict__ twi)
+{
+    using Lay = Layout<LOGN>;
+    constexpr int N = Lay::N, T = Lay::T;
+    const uint32_t p = c_pc.p[g], pinv = c_pc.pinv_neg[g];
+    ntt_forward<LOGN, 4>(d, buf, tau, twf, p, 1 + g);
+
+    uint32_t o[2][16];
+    const uint4 *kp = reinterpret_cast<const uint4 *>(key + (size_t)tau * 8);
+    uint4 ka = __ldg(kp), kb = __ldg(kp + 1);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        uint4 na, nb;
+        if (q + 1 < 16) {
+            const uint4 *np = kp + (size_t)(q + 1) * T * 2;
+            na = __ldg(np);
+            nb = __ldg(np + 1);
+        }
+        const uint32_t d0 = csub(csub(d[0][q], 2 * p), p);
+        const uint32_t d1 = csub(csub(d[1][q], 2 * p), p);
+        const uint32_t d2 = csub(csub(d[2][q], 2 * p), p);
+        const uint32_t d3 = csub(csub(d[3][q], 2 * p), p);
+        // slot = row * 2 + column
+        const uint64_t t0 = (uint64_t)d0 * ka.x + (uint64_t)d1 * ka.z + (uint64_t)d2 * kb.x + (uint64_t)d3 * kb.z;
+        const uint64_t t1 = (uint64_t)d0 * ka.y + (uint64_t)d1 * ka.w + (uint64_t)d2 * kb.y + (uint64_t)d3 * kb.w;
+        o[0][q] = redc(t0, p, pinv);
+        o[1][q] = redc(t1, p, pinv);
+        if (q + 1 < 16) { ka = na; kb = nb; }
+    }
+    ntt_inverse<LOGN, 2>(o, buf, tau, twi, p, 1 + g);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const uint32_t e = tau | ((uint32_t)q << Lay::B0);
+        crt[(g * 2 + 0) * N + e] = csub(o[0][q], p);
+        crt[(g * 2 + 1) * N + e] = csub(o[1][q], p);
+    }
+}
+
+// ---------------------------------------------------------------- blind rotation
+template <int LOGN>
+struct BrSmem {
+    static constexpr int N = 1 << LOGN;
+    static constexpr size_t acc_bytes = 2 * N * sizeof(uint64_t);
+    static constexpr size_t buf_bytes = 3 * 4 * N * sizeof(uint32_t);
+    static constexpr size_t crt_bytes = 3 * 2 * N * sizeof(uint32_t);
+    static constexpr size_t total = acc_bytes + buf_bytes + crt_bytes;
+};
+
+template <int LOGN>
+__global__ void __launch_bounds__(3 * (1 << LOGN) / 16, 1)
+k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__restrict__ ms, uint32_t n, const uint32_t *__restrict__ bsk,
+               const uint2 *__restrict__ tw, const uint8_t *__restrict__ luts, int lut_per_job,
+               uint32_t base_log)
+{
+    using Lay = Layout<LOGN>;
+    constexpr int N = Lay::N, T = Lay::T, NT = 3 * T;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    uint64_t *acc = reinterpret_cast<uint64_t *>(smem_raw);
+    uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw + BrSmem<LOGN>::acc_bytes);
+    uint32_t *crt = bufs + 3 * 4 * N;
+
+    const int tid = threadIdx.x;
+    const int g = tid / T;
+    const uint32_t tau = tid % T;
+    uint32_t *buf = bufs + g * 4 * N;
+    const uint32_t p = c_pc.p[g];
+    const uint2 *twf = tw + (size_t)(g * 2 + 0) * N;
+    const uint2 *twi = tw + (size_t)(g * 2 + 1) * N;
+    const uint32_t B = 1u << base_log, hB = B >> 1;
+    const uint32_t shift = 64 - 2 * base_log;
+    const uint64_t round = 1ull << (shift - 1);
+    const size_t key_row = (size_t)3 * 16 * T * 8;   // u32 per BSK index i
+
+    for (uint32_t job = blockIdx.x; job < njobs; job += gridDim.x) {
+        const Job J = jobs[job];
+        const uint32_t *msj = ms + (size_t)job * (n + 1);
+        uint8_t f[16];
+        {
+            const uint8_t *lp = luts + (lut_per_job ? (size_t)job * 16 : (size_t)J.lut * 16);
+            const uint4 lv = *reinterpret_cast<const uint4 *>(lp);
+            memcpy(f, &lv, 16);
+        }
+        // ACC = (0, X^{-b} v')
+        const uint32_t b = __ldg(msj + n);
+        for (int e = tid; e < N; e += NT) {
+            acc[e] = 0;
+            acc[N + e] = test_poly_at<LOGN>(f, (e + b) & (2 * N - 1));
+        }
+        __syncthreads();
+
+        for (uint32_t i = 0; i < n; ++i) {
+            const uint32_t a = __ldg(msj + i);
+            if (a == 0) continue;   // X^0 ACC - ACC = 0: the external product is exactly 0
+            // decomposition of X^a ACC - ACC into 2 balanced digits per coefficient
+            uint32_t d[4][16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const uint32_t e = tau | ((uint32_t)q << Lay::B0);
+                const uint32_t idx = (e - a) & (2 * N - 1);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const uint64_t cur = acc[j * N + e];
+                    uint64_t rv = acc[j * N + (idx & (N - 1))];
+                    if (idx >= (uint32_t)N) rv = 0 - rv;
+                    const uint64_t x = rv - cur;
+                    const uint64_t v = (x + round) >> shift;
+                    const uint32_t u2 = (uint32_t)v & (B - 1), u1 = (uint32_t)(v >> base_log) & (B - 1);
+                    const uint32_t c2 = u2 >= hB;
+                    const int32_t d2 = (int32_t)u2 - (int32_t)(c2 * B);
+                    const uint32_t r1 = u1 + c2;
+                    const int32_t d1 = (int32_t)r1 - (int32_t)((r1 >= hB) * B);
+                    d[2 * j + 0][q] = d1 < 0 ? (uint32_t)(d1 + (int32_t)p) : (uint32_t)d1;
+                    d[2 * j + 1][q] = d2 < 0 ? (uint32_t)(d2 + (int32_t)p) : (uint32_t)d2;
+                }
+            }
+            ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 16 * T * 8, buf, crt, tau, g,
+                                   twf, twi);
+            __syncthreads();
+            for (int c = tid; c < 2 * N; c += NT) {
+                const int j = c >> LOGN, e = c & (N - 1);
+                const uint64_t x = crt3(crt[(0 * 2 + j) * N + e], crt[(1 * 2 + j) * N + e],
+                                        crt[(2 * 2 + j) * N + e], c_pc);
+                acc[j * N + e] += x;
+            }
+            __syncthreads();
+        }
+
+        // sample extract (coefficient 0) and epilogue
+        uint64_t *o0 = J.dst[0];
+        uint64_t *o1 = J.dst[1];
+        for (int u = tid; u <= N; u += NT) {
+            uint64_t val;
+            if (u == N) val = acc[N];
+            else if (u == 0) val = acc[0];
+            else val = 0 - acc[N - u];
+            if (J.kind == JOB_CELL) {
+                const uint64_t vold = o0[u], hold = o1[u];
+                o0[u] = val - hold;   // v[i][j] = M - h[i-1][j]
+                o1[u] = val - vold;   // h[i][j] = M - v[i][j-1]
+            } else {
+                o0[u] = val;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- key switch
+constexpr int KS_TJ = 16;       // jobs per CTA
+constexpr int KS_THREADS = 128; // output columns per CTA
+constexpr int KS_UCH = 128;     // input coefficients per digit chunk
+constexpr int KS_MAXL = 8;
+
+__global__ void __launch_bounds__(KS_THREADS)
+k_keyswitch(const Job *__restrict__ jobs, uint32_t njobs,
+            const uint64_t *__restrict__ ksk, uint32_t n, uint32_t big, uint32_t ks_level, uint32_t ks_base_log,
+            uint32_t log2_2N, uint32_t *__restrict__ ms)
+{
+    __shared__ __align__(16) int8_t dig[KS_UCH][KS_MAXL][KS_TJ];
+    __shared__ Job sj[KS_TJ];
+    const int t = threadIdx.x;
+    const uint32_t j0 = blockIdx.x * KS_TJ;
+    const uint32_t c = blockIdx.y * KS_THREADS + t;
+    if (t < KS_TJ) {
+        if (j0 + t < njobs) sj[t] = jobs[j0 + t];
+        else {
+            Job z{};
+            sj[t] = z;
+        }
+    }
+    __syncthreads();
+
+    const uint32_t beta = ks_level * ks_base_log;
+    const uint64_t rnd = 1ull << (63 - beta);
+    const uint32_t Bk = 1u << ks_base_log, hBk = Bk >> 1;
+    uint64_t acc[KS_TJ];
+#pragma unroll
+    for (int jj = 0; jj < KS_TJ; ++jj) acc[jj] = 0;
+
+    for (uint32_t u0 = 0; u0 < big; u0 += KS_UCH) {
+        const uint32_t u = u0 + t;
+#pragma unroll 1
+        for (int jj = 0; jj < KS_TJ; ++jj) {
+            uint64_t a = 0;
+            if (u < big) {
+#pragma unroll
+                for (int s = 0; s < 3; ++s)
+                    if (sj[jj].src[s])
+                        a += (uint64_t)(int64_t)sj[jj].coef[s] * __ldg(sj[jj].src[s] + u);
+            }
+            const uint64_t v = (a + rnd) >> (64 - beta);
+            uint32_t carry = 0;
+            for (int lev = (int)ks_level; lev >= 1; --lev) {
+                const uint32_t uu = (uint32_t)(v >> ((ks_level - lev) * ks_base_log)) & (Bk - 1);
+                const uint32_t r = uu + carry;
+                carry = r >= hBk;
+                dig[t][lev - 1][jj] = (int8_t)((int32_t)r - (int32_t)(carry * Bk));
+            }
+        }
+        __syncthreads();
+        if (c <= n) {
+            const uint32_t ucount = min((uint32_t)KS_UCH, big - u0);
+            for (uint32_t ul = 0; ul < ucount; ++ul) {
+                const uint64_t *krow = ksk + ((size_t)(u0 + ul) * ks_level) * (n + 1) + c;
+                for (uint32_t lev = 0; lev < ks_level; ++lev) {
+                    const uint64_t kv = __ldg(krow + (size_t)lev * (n + 1));
+                    const int4 dv = *reinterpret_cast<const int4 *>(&dig[ul][lev][0]);
+                    const int32_t w[4] = {dv.x, dv.y, dv.z, dv.w};
+#pragma unroll
+                    for (int jj = 0; jj < KS_TJ; ++jj) {
+                        const int32_t dd = (int32_t)(int8_t)(w[jj >> 2] >> ((jj & 3) * 8));
+                        acc[jj] += (uint64_t)(int64_t)dd * kv;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (c > n) return;
+    const uint32_t twoN_mask = (1u << log2_2N) - 1;
+#pragma unroll 1
+    for (int jj = 0; jj < KS_TJ; ++jj) {
+        const uint32_t j = j0 + jj;
+        if (j >= njobs) break;
+        uint64_t val = 0 - acc[jj];
+        if (c == n) {
+            uint64_t bb = (uint64_t)(sj[jj].cst & 31) << kDeltaLog;
+            for (int s = 0; s < 3; ++s)
+                if (sj[jj].src[s])
+                    bb += (uint64_t)(int64_t)sj[jj].coef[s] * sj[jj].src[s][big];
+            val += bb;
+        }
+        ms[(size_t)j * (n + 1) + c] =
+            (uint32_t)((val + (1ull << (63 - log2_2N))) >> (64 - log2_2N)) & twoN_mask;
+    }
+}
+
+// ---------------------------------------------------------------- key conversion
+// BSK (coefficient domain, [i][row][col][N] u64) -> NTT domain
+// out[i][g][q][tau][slot = row*2+col] = NTT_p(row,col)[pos(tau,q)] * R * N^{-1} mod p
+template <int LOGN>
+__global__ void __launch_bounds__(3 * (1 << LOGN) / 16)
+k_bsk_to_ntt(const uint64_t *__restrict__ coef, uint32_t count, uint32_t *__restrict__ out,
+             const uint2 *__restrict__ tw, uint32_t m0, uint32_t ms0, uint32_t m1, uint32_t ms1, uint32_t m2,
+             uint32_t ms2)
+{
+    using Lay = Layout<LOGN>;
+    constexpr int N = Lay::N, T = Lay::T;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw);
+    const int tid = threadIdx.x, g = tid / T;
+    const uint32_t tau = tid % T;
+    const uint32_t i = blockIdx.x, h = blockIdx.y;   // h: slots 4h..4h+3
+    if (i >= count) return;
+    const uint32_t p = c_pc.p[g];
+    uint32_t v[4][16];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t slot = 4 * h + k;   // = row * 2 + col
+        const uint64_t *src = coef + ((size_t)i * 8 + slot) * N;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const uint32_t e = tau | ((uint32_t)q << Lay::B0);
+            v[k][q] = residue_of_signed((int64_t)src[e], p);
+        }
+    }
+    ntt_forward<LOGN, 4>(v, bufs + g * 4 * N, tau, tw + (size_t)(g * 2) * N, p, 1 + g);
+    const uint32_t m = g == 0 ? m0 : (g == 1 ? m1 : m2), msh = g == 0 ? ms0 : (g == 1 ? ms1 : ms2);
+    uint32_t *dst = out + (size_t)i * 3 * 16 * T * 8 + (size_t)g * 16 * T * 8 + (size_t)tau * 8 + 4 * h;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t x = csub(csub(v[k][q], 2 * p), p);
+            dst[(size_t)q * T * 8 + k] = csub(mul_shoup(m, msh, x, p), p);
+        }
+    }
+}
+
+// Product-only kernel (parity of the NTT/CRT path): out[item] = sum_r dig[r] * key[r][col]
+template <int LOGN>
+__global__ void __launch_bounds__(3 * (1 << LOGN) / 16, 1)
+k_poly_mul(const int32_t *__restrict__ dig, const uint32_t *__restrict__ keyntt, uint64_t *__restrict__ out,
+           uint32_t count, const uint2 *__restrict__ tw)
+{
+    using Lay = Layout<LOGN>;
+    constexpr int N = Lay::N, T = Lay::T, NT = 3 * T;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw + BrSmem<LOGN>::acc_bytes);
+    uint32_t *crt = bufs + 3 * 4 * N;
+    const int tid = threadIdx.x, g = tid / T;
+    const uint32_t tau = tid % T;
+    const uint32_t item = blockIdx.x;
+    if (item >= count) return;
+    const uint32_t p = c_pc.p[g];
+    uint32_t d[4][16];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const uint32_t e = tau | ((uint32_t)q << Lay::B0);
+            const int32_t x = dig[((size_t)item * 4 + r) * N + e];
+            d[r][q] = x < 0 ? (uint32_t)(x + (int32_t)p) : (uint32_t)x;
+        }
+    ext_product_core<LOGN>(d, keyntt + (size_t)item * 3 * 16 * T * 8 + (size_t)g * 16 * T * 8,
+                           bufs + g * 4 * N, crt, tau, g, tw + (size_t)(g * 2) * N, tw + (size_t)(g * 2 + 1) * N);
+    __syncthreads();
+    for (int c = tid; c < 2 * N; c += NT) {
+        const int j = c >> LOGN, e = c & (N - 1);
+        out[((size_t)item * 2 + j) * N + e] =
+            crt3(crt[(0 * 2 + j) * N + e], crt[(1 * 2 + j) * N + e], crt[(2 * 2 + j) * N + e], c_pc);
+    }
+}
+
+// ---------------------------------------------------------------- small helpers
+__global__ void k_fill_trivial(uint64_t *arena, size_t stride, uint32_t big, size_t first, uint32_t count,
+                               uint64_t body)
+{
+    const uint32_t s = blockIdx.x;
+    if (s >= count) return;
+    uint64_t *row = arena + (first + s) * stride;
+    for (uint32_t u = threadIdx.x; u <= big; u += blockDim.x) row[u] = u == big ? body : 0;
+}
+
+}  // namespace dev
+
+// ---------------------------------------------------------------- host wrappers
+using namespace dev;
+
+int br_threads(uint32_t N) { return 3 * (int)N / 16; }
+int br_smem_bytes(uint32_t N) { return N == 2048 ? (int)BrSmem<11>::total : (int)BrSmem<9>::total; }
+size_t bsk_ntt_words(uint32_t n, uint32_t N) { return (size_t)n * 3 * 16 * (N / 16) * 8; }
+
+cudaError_t upload_prime_consts(const PrimeConsts &pc) { return cudaMemcpyToSymbol(c_pc, &pc, sizeof(pc)); }
+
+template <int LOGN>
+static cudaError_t set_attrs()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_blind_rotate<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)BrSmem<LOGN>::total);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_poly_mul<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BrSmem<LOGN>::total);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_bsk_to_ntt<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(3 * 4 * (1 << LOGN) * sizeof(uint32_t)));
+}
+
+cudaError_t prepare_kernels(uint32_t N) { return N == 2048 ? set_attrs<11>() : set_attrs<9>(); }
+
+int br_blocks_per_sm(uint32_t N)
+{
+    int nb = 0;
+    cudaError_t e = N == 2048
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate<11>, br_threads(N), BrSmem<11>::total)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate<9>, br_threads(N), BrSmem<9>::total);
+    if (e != cudaSuccess) { cudaGetLastError(); return 1; }
+    return nb;
+}
+
+cudaError_t launch_bsk_to_ntt_count(uint32_t N, const uint64_t *coef, uint32_t count, uint32_t *out,
+                                    const uint32_t *tw, const uint32_t mont[3][2], cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    dim3 grid(count, 2);
+    const uint2 *t2 = reinterpret_cast<const uint2 *>(tw);
+    const size_t sm = 3 * 4 * N * sizeof(uint32_t);
+    if (N == 2048)
+        k_bsk_to_ntt<11><<<grid, br_threads(N), sm, s>>>(coef, count, out, t2, mont[0][0], mont[0][1], mont[1][0],
+                                                          mont[1][1], mont[2][0], mont[2][1]);
+    else
+        k_bsk_to_ntt<9><<<grid, br_threads(N), sm, s>>>(coef, count, out, t2, mont[0][0], mont[0][1], mont[1][0],
+                                                         mont[1][1], mont[2][0], mont[2][1]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keyswitch(const lvs_ctx *ctx, const Job *jobs, size_t njobs, uint32_t *ms, cudaStream_t s)
+{
+    if (njobs == 0) return cudaSuccess;
+    const auto &p = ctx->P.p;
+    dim3 grid((unsigned)((njobs + KS_TJ - 1) / KS_TJ), (p.n + 1 + KS_THREADS - 1) / KS_THREADS);
+    const uint32_t log2_2N = ctx->P.log_n() + 1;
+    k_keyswitch<<<grid, KS_THREADS, 0, s>>>(jobs, (uint32_t)njobs, ctx->ksk, p.n, ctx->P.big(), p.ks_level,
+                                             p.ks_base_log, log2_2N, ms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blind_rotate(const lvs_ctx *ctx, const Job *jobs, size_t njobs, const uint32_t *ms,
+                                const uint8_t *luts, int lut_per_job, cudaStream_t s)
+{
+    if (njobs == 0) return cudaSuccess;
+    const auto &p = ctx->P.p;
+    const unsigned grid = (unsigned)std::min<size_t>(njobs, (size_t)ctx->br_grid);
+    const uint2 *t2 = reinterpret_cast<const uint2 *>(ctx->tw);
+    if (p.N == 2048)
+        k_blind_rotate<11><<<grid, br_threads(p.N), BrSmem<11>::total, s>>>(
+            jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log);
+    else
+        k_blind_rotate<9><<<grid, br_threads(p.N), BrSmem<9>::total, s>>>(
+            jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poly_mul(const lvs_ctx *ctx, const int32_t *dig, const uint32_t *keyntt, uint64_t *out,
+                            size_t count, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    const uint32_t N = ctx->P.p.N;
+    const uint2 *t2 = reinterpret_cast<const uint2 *>(ctx->tw);
+    if (N == 2048)
+        k_poly_mul<11><<<(unsigned)count, br_threads(N), BrSmem<11>::total, s>>>(dig, keyntt, out, (uint32_t)count, t2);
+    else
+        k_poly_mul<9><<<(unsigned)count, br_threads(N), BrSmem<9>::total, s>>>(dig, keyntt, out, (uint32_t)count, t2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_trivial(uint64_t *arena, size_t stride, uint32_t big, size_t first, size_t count,
+                                uint64_t body, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    k_fill_trivial<<<(unsigned)count, 256, 0, s>>>(arena, stride, big, first, (uint32_t)count, body);
+    return cudaGetLastError();
+}
+
+}  // namespace lvs

@@ -1,0 +1,191 @@
+// Internal declarations of the GB300 Leuvenshtein library (not part of the ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lvs.h"
+
+namespace lvs {
+
+// ----------------------------------------------------------------- errors
+lvs_status set_error(lvs_status st, const std::string &msg);
+lvs_status cuda_error(cudaError_t e, const char *what);
+#define LVS_CUDA(call)                                                        \
+    do {                                                                      \
+        cudaError_t e__ = (call);                                             \
+        if (e__ != cudaSuccess) return ::lvs::cuda_error(e__, #call);         \
+    } while (0)
+
+// ----------------------------------------------------------------- constants
+constexpr int kPrimes = 3;
+// Three NTT primes p = c * 2^12 + 1 < 2^30 (2N-th roots of unity exist for
+// N <= 2048; 4p < 2^32 allows lazy butterflies).  Their product M > 2^89
+// bounds the exact integer external product (|coef| <= 4 * N * 2^12 * 2^63).
+constexpr uint32_t kPrime[kPrimes] = {0x3fff4001u, 0x3ffee001u, 0x3ffeb001u};
+constexpr int kDeltaLog = 59;      // q / 32
+constexpr int kRows = 4;           // (k+1) * pbs_level with k = 1, level = 2
+constexpr int kMaxJobsPerLaunch = 1 << 20;
+
+// LUT ids in the context's LUT table
+enum : uint8_t { LUT_EQ = 0, LUT_EQ9 = 1, LUT_MIN = 2, LUT_USER0 = 8 };
+// job kinds (epilogue of the blind-rotation kernel)
+enum : uint8_t { JOB_STORE = 0, JOB_CELL = 1 };
+
+// One PBS of a wavefront launch.  Input = sum_s coef[s] * (*src[s]) +
+// cst * Delta, a linear combination of big ciphertexts (Section 2.2 linear
+// operations); output written by the epilogue `kind`:
+//   STORE: *dst[0] = PBS
+//   CELL : M = PBS; *dst[0] (v) = M - *dst[1]_old (h),
+//                   *dst[1] (h) = M - *dst[0]_old (v)      (Section 3.1.1)
+// All pointers are device rows of k*N+1 words.
+struct alignas(16) Job {
+    const uint64_t *src[3];
+    uint64_t *dst[2];
+    int8_t coef[3];
+    int8_t cst;
+    uint8_t lut;
+    uint8_t kind;
+    uint8_t pad[2];
+};
+static_assert(sizeof(Job) == 48, "Job layout");
+
+// ----------------------------------------------------------------- host keys
+struct Params {
+    lvs_params p;
+    uint32_t big() const { return p.k * p.N; }
+    uint32_t log_n() const { uint32_t l = 0; while ((1u << l) < p.N) ++l; return l; }
+    size_t bsk_words() const { return (size_t)p.n * (p.k + 1) * p.pbs_level * (p.k + 1) * p.N; }
+    size_t ksk_words() const { return (size_t)p.k * p.N * p.ks_level * (p.n + 1); }
+};
+lvs_status check_params(const lvs_params &p);
+
+}  // namespace lvs
+
+struct lvs_client_key {
+    lvs::Params P;
+    std::vector<uint64_t> lwe_key;   // n
+    std::vector<uint64_t> glwe_key;  // k*N
+};
+
+struct lvs_server_key {
+    lvs::Params P;
+    std::vector<uint64_t> bsk;  // coefficient domain
+    std::vector<uint64_t> ksk;
+};
+
+struct lvs_ct_string {
+    lvs_alphabet alphabet;
+    uint32_t symbols;   // per character
+    uint32_t big;       // k*N
+    size_t len;         // characters
+    std::vector<uint64_t> data;  // [len][symbols][big+1]
+    uint64_t *d = nullptr;       // optional device copy, rows of `dstride` words
+    size_t dstride = 0;
+    int ddevice = -1;
+};
+
+namespace lvs {
+uint32_t symbols_per_char(lvs_alphabet a);
+// character -> (symbol values); returns false if outside the alphabet
+bool encode_char(lvs_alphabet a, uint8_t c, uint32_t sym[2]);
+uint32_t alphabet_size(lvs_alphabet a);
+uint8_t alphabet_char(lvs_alphabet a, uint32_t idx);
+void encrypt_lwe(const lvs_client_key &ck, uint32_t value, uint64_t seed, uint64_t i0, uint64_t i1,
+                 uint64_t *ct);
+uint32_t decrypt_lwe(const lvs_client_key &ck, const uint64_t *ct);
+
+struct Timing {
+    bool enabled = false;
+    // one launch step: key switch between a and b, blind rotation between b and c
+    struct Pending { cudaEvent_t a, b, c; uint64_t items; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    lvs_kernel_stats stats[2] = {};
+};
+
+}  // namespace lvs
+
+struct lvs_ctx {
+    lvs::Params P;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    int br_grid = 0;
+    // device keys
+    uint32_t *bsk_ntt = nullptr;   // [n][kPrimes][16][T][8] u32
+    uint64_t *ksk = nullptr;       // [kN][ks_l][n+1]
+    uint32_t *tw = nullptr;        // twiddles: uint2 {w, w_shoup} [prime][fwd, inv][N]
+    uint8_t *luts = nullptr;       // [256][16]
+    // scratch (grown on demand; owned by the context)
+    uint32_t *ms = nullptr;        // [ms_cap][n+1] modulus-switched masks of one launch
+    size_t ms_cap = 0;
+    lvs::Job *jobs = nullptr;      // [jobs_cap] jobs of a whole run
+    size_t jobs_cap = 0;
+    uint64_t pbs_done = 0;
+    uint64_t launches = 0;
+    lvs::Timing timing;
+    struct GraphRun { cudaGraphExec_t exec; cudaEvent_t done; };
+    std::vector<GraphRun> graphs;  // launched graphs, destroyed once complete
+    std::mutex mu;
+};
+
+struct lvs_result {
+    lvs::Params P;
+    int device = 0;
+    uint64_t *d = nullptr;            // device rows [total][stride], owned
+    size_t stride = 0;                // words per row (>= k*N+1)
+    struct Item { size_t m, n, first, count; };
+    std::vector<Item> items;
+    bool is_eq = false;
+    cudaEvent_t done = nullptr;       // recorded after the producing launches
+};
+
+struct lvs_eq_table {
+    lvs::Params P;
+    int device = 0;
+    lvs_alphabet alphabet = LVS_ALPHA_ASCII7;
+    size_t len = 0;                   // characters of the encrypted string
+    std::vector<uint8_t> subset;      // plaintext characters, one table row each
+    int32_t row_of[256];              // character -> row, -1 if absent
+    uint64_t *d = nullptr;            // device rows [nsub][len][stride], owned
+    size_t stride = 0;
+    cudaEvent_t done = nullptr;
+};
+
+namespace lvs {
+namespace dev { struct PrimeConsts; }
+// kernel launch wrappers (kernels.cu)
+cudaError_t upload_prime_consts(const dev::PrimeConsts &pc);
+cudaError_t prepare_kernels(uint32_t N);
+cudaError_t launch_bsk_to_ntt_count(uint32_t N, const uint64_t *coef, uint32_t count, uint32_t *out,
+                                    const uint32_t *tw, const uint32_t mont[3][2], cudaStream_t s);
+cudaError_t launch_keyswitch(const lvs_ctx *ctx, const Job *jobs, size_t njobs, uint32_t *ms, cudaStream_t s);
+cudaError_t launch_blind_rotate(const lvs_ctx *ctx, const Job *jobs, size_t njobs, const uint32_t *ms,
+                                const uint8_t *luts, int lut_per_job, cudaStream_t s);
+cudaError_t launch_poly_mul(const lvs_ctx *ctx, const int32_t *dig, const uint32_t *keyntt, uint64_t *out,
+                            size_t count, cudaStream_t s);
+cudaError_t launch_fill_trivial(uint64_t *arena, size_t stride, uint32_t big, size_t first, size_t count,
+                                uint64_t body, cudaStream_t s);
+int br_smem_bytes(uint32_t N);
+int br_threads(uint32_t N);
+size_t bsk_ntt_words(uint32_t n, uint32_t N);
+
+// host tables (tables.cu)
+void make_twiddles(uint32_t N, std::vector<uint32_t> &out);
+void make_prime_consts(dev::PrimeConsts &pc);
+void make_mont(uint32_t N, uint32_t mont[3][2]);
+void make_luts(std::vector<uint8_t> &table);   // [256][16]
+
+// scratch and timing (ctx.cu)
+lvs_status ensure_scratch(lvs_ctx *ctx, size_t njobs_total, size_t njobs_step);
+lvs_status run_steps(lvs_ctx *ctx, const std::vector<Job> &jobs, const std::vector<size_t> &step_off,
+                     bool use_graph);
+void timing_collect(lvs_ctx *ctx);
+}  // namespace lvs

@@ -1,0 +1,230 @@
+// Device arithmetic of the exact negacyclic product mod 2^64 used by the
+// blind rotation (the external product GGSW [x] GLWE of TFHE, Section 2.2 of
+// the paper defers to the standard TFHE construction).
+//
+// The integer product of a digit polynomial (|d| <= B/2) and a key polynomial
+// (signed 64-bit) has coefficients below 2^88 in magnitude, so it is computed
+// exactly modulo three 30-bit NTT primes and rebuilt by CRT (Garner), then
+// reduced mod 2^64.  Per prime: merged negacyclic number-theoretic transform
+// (Cooley-Tukey forward, natural order in / bit-reversed out; Gentleman-Sande
+// inverse), with Harvey's lazy butterflies (values kept in [0, 4p)) and
+// Shoup's precomputed-quotient modular multiplication by constants;
+// Montgomery reduction (R = 2^32) for the key product, whose key operand is
+// stored pre-multiplied by R * N^{-1} so the inverse transform needs no scaling.
+//
+// Register layout: a prime group of T = N/16 threads holds 16 coefficients per
+// thread of several polynomials.  An N-point transform runs as three register
+// passes of <= 4 radix-2 stages:
+//   L0: e = tau | q << (logN-4)           stages 0..3
+//   L1: e = hi << (logN-4) | q << (logN-8) | lo,   tau = hi << (logN-8) | lo
+//                                          stages 4..7
+//   L2: e = tau << 4 | q                   stages 8..logN-1
+// with shared-memory exchanges between passes, addressed through the swizzle
+// e ^ ((e >> 4) & 31), which is bank-conflict free for all three layouts.
+// L1 <-> L2 exchanges stay inside a warp; L0 <-> L1 needs the group barrier.
+#pragma once
+#include <cstdint>
+
+namespace lvs {
+namespace dev {
+
+struct PrimeConsts {
+    uint32_t p[3];
+    uint32_t pinv_neg[3];      // -p^{-1} mod 2^32
+    uint32_t mont[3];          // R * N^{-1} mod p (for key conversion)
+    uint32_t mont_sh[3];       // Shoup companion of mont
+    uint32_t r2[3];            // R^2 mod p (unused by the hot path)
+    // Garner: x = v0 + p0 v1 + p0 p1 v2
+    uint32_t c01, c01_sh;      // p0^{-1} mod p1
+    uint32_t p0m2, p0m2_sh;    // p0 mod p2
+    uint32_t c012, c012_sh;    // (p0 p1)^{-1} mod p2
+    uint64_t p01;              // p0 p1 mod 2^64
+    uint64_t m64;              // p0 p1 p2 mod 2^64
+    uint32_t half2;            // p2 >> 1
+};
+
+__device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m)
+{
+    // x in [0, 2m) -> [0, m)
+    return min(x, x - m);
+}
+
+// w * x mod p in [0, 2p) for any x < 2^32 (Shoup)
+__device__ __forceinline__ uint32_t mul_shoup(uint32_t w, uint32_t wsh, uint32_t x, uint32_t p)
+{
+    const uint32_t q = __umulhi(wsh, x);
+    return w * x - q * p;
+}
+
+// Montgomery reduction of T < p * 2^32: T * 2^-32 mod p in [0, 2p)
+__device__ __forceinline__ uint32_t redc(uint64_t T, uint32_t p, uint32_t pinv_neg)
+{
+    const uint32_t m = (uint32_t)T * pinv_neg;
+    return (uint32_t)((T + (uint64_t)m * p) >> 32);
+}
+
+__device__ __forceinline__ uint32_t swz(uint32_t e) { return e ^ ((e >> 4) & 31u); }
+
+__device__ __forceinline__ void group_bar(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <int LOGN>
+struct Layout {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int T = N / 16;
+    static constexpr int B0 = LOGN - 4;   // L0 register stride exponent
+    static constexpr int B1 = LOGN - 8;   // L1 register stride exponent
+    static constexpr int S2 = LOGN - 8;   // stages in the last pass
+    __device__ static __forceinline__ uint32_t base0(uint32_t tau) { return tau; }
+    __device__ static __forceinline__ uint32_t base1(uint32_t tau)
+    {
+        return ((tau >> B1) << (B1 + 4)) | (tau & ((1u << B1) - 1u));
+    }
+    __device__ static __forceinline__ uint32_t base2(uint32_t tau) { return tau << 4; }
+};
+
+// One register pass of forward (Cooley-Tukey) stages s0 .. s0+cnt-1 on NP
+// polynomials that share positions (and hence twiddles).
+template <int LOGN, int B, int S0, int CNT, int NP>
+__device__ __forceinline__ void fwd_pass(uint32_t (&v)[NP][16], uint32_t base, const uint2 *__restrict__ tw,
+                                         uint32_t p)
+{
+    const uint32_t p2 = 2 * p;
+#pragma unroll
+    for (int si = 0; si < CNT; ++si) {
+        const int s = S0 + si;
+        const int rb = LOGN - s - 1 - B;
+#pragma unroll
+        for (int g = 0; g < (1 << (3 - rb)); ++g) {
+            const uint32_t eg = base | ((uint32_t)(g << (rb + 1)) << B);
+            const uint2 w = __ldg(tw + (1u << s) + (eg >> (LOGN - s)));
+#pragma unroll
+            for (int low = 0; low < (1 << rb); ++low) {
+                const int q0 = (g << (rb + 1)) | low, q1 = q0 | (1 << rb);
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    const uint32_t x = csub(v[k][q0], p2);
+                    const uint32_t t = mul_shoup(w.x, w.y, v[k][q1], p);
+                    v[k][q0] = x + t;
+                    v[k][q1] = x - t + p2;
+                }
+            }
+        }
+    }
+}
+
+// One register pass of inverse (Gentleman-Sande) stages s0+cnt-1 .. s0.
+template <int LOGN, int B, int S0, int CNT, int NP>
+__device__ __forceinline__ void inv_pass(uint32_t (&v)[NP][16], uint32_t base, const uint2 *__restrict__ tw,
+                                         uint32_t p)
+{
+    const uint32_t p2 = 2 * p;
+#pragma unroll
+    for (int si = CNT - 1; si >= 0; --si) {
+        const int s = S0 + si;
+        const int rb = LOGN - s - 1 - B;
+#pragma unroll
+        for (int g = 0; g < (1 << (3 - rb)); ++g) {
+            const uint32_t eg = base | ((uint32_t)(g << (rb + 1)) << B);
+            const uint2 w = __ldg(tw + (1u << s) + (eg >> (LOGN - s)));
+#pragma unroll
+            for (int low = 0; low < (1 << rb); ++low) {
+                const int q0 = (g << (rb + 1)) | low, q1 = q0 | (1 << rb);
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    const uint32_t x = v[k][q0], y = v[k][q1];
+                    v[k][q0] = csub(x + y, p2);
+                    v[k][q1] = mul_shoup(w.x, w.y, x - y + p2, p);
+                }
+            }
+        }
+    }
+}
+
+// store / load the NP polynomials of a thread in layout (B, base) to/from
+// buf[k * N + swz(e)]
+template <int LOGN, int B, int NP>
+__device__ __forceinline__ void st_layout(uint32_t *buf, const uint32_t (&v)[NP][16], uint32_t base)
+{
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const uint32_t a = swz(base | ((uint32_t)q << B));
+#pragma unroll
+        for (int k = 0; k < NP; ++k) buf[k * (1 << LOGN) + a] = v[k][q];
+    }
+}
+
+template <int LOGN, int B, int NP>
+__device__ __forceinline__ void ld_layout(const uint32_t *buf, uint32_t (&v)[NP][16], uint32_t base)
+{
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const uint32_t a = swz(base | ((uint32_t)q << B));
+#pragma unroll
+        for (int k = 0; k < NP; ++k) v[k][q] = buf[k * (1 << LOGN) + a];
+    }
+}
+
+// Full forward transform of NP polynomials held in L0 layout; returns them in
+// L2 layout (bit-reversed evaluation order), values in [0, 4p).
+// buf: NP * N words of this group's shared memory.  bar_id: group barrier.
+template <int LOGN, int NP>
+__device__ __forceinline__ void ntt_forward(uint32_t (&v)[NP][16], uint32_t *buf, uint32_t tau,
+                                            const uint2 *__restrict__ tw, uint32_t p, int bar_id)
+{
+    using Lay = Layout<LOGN>;
+    fwd_pass<LOGN, Lay::B0, 0, 4, NP>(v, Lay::base0(tau), tw, p);
+    __syncwarp();
+    st_layout<LOGN, Lay::B0, NP>(buf, v, Lay::base0(tau));
+    if (Lay::T > 32) group_bar(bar_id, Lay::T); else __syncwarp();
+    ld_layout<LOGN, Lay::B1, NP>(buf, v, Lay::base1(tau));
+    fwd_pass<LOGN, Lay::B1, 4, 4, NP>(v, Lay::base1(tau), tw, p);
+    __syncwarp();
+    st_layout<LOGN, Lay::B1, NP>(buf, v, Lay::base1(tau));
+    __syncwarp();
+    ld_layout<LOGN, 0, NP>(buf, v, Lay::base2(tau));
+    fwd_pass<LOGN, 0, 8, Lay::S2, NP>(v, Lay::base2(tau), tw, p);
+}
+
+// Inverse transform of NP polynomials held in L2 layout (values in [0, 2p));
+// returns them in L0 layout (natural order), values in [0, 2p), NOT scaled by
+// N^{-1}.
+template <int LOGN, int NP>
+__device__ __forceinline__ void ntt_inverse(uint32_t (&v)[NP][16], uint32_t *buf, uint32_t tau,
+                                            const uint2 *__restrict__ tw, uint32_t p, int bar_id)
+{
+    using Lay = Layout<LOGN>;
+    inv_pass<LOGN, 0, 8, Lay::S2, NP>(v, Lay::base2(tau), tw, p);
+    __syncwarp();
+    st_layout<LOGN, 0, NP>(buf, v, Lay::base2(tau));
+    __syncwarp();
+    ld_layout<LOGN, Lay::B1, NP>(buf, v, Lay::base1(tau));
+    inv_pass<LOGN, Lay::B1, 4, 4, NP>(v, Lay::base1(tau), tw, p);
+    __syncwarp();
+    st_layout<LOGN, Lay::B1, NP>(buf, v, Lay::base1(tau));
+    if (Lay::T > 32) group_bar(bar_id, Lay::T); else __syncwarp();
+    ld_layout<LOGN, Lay::B0, NP>(buf, v, Lay::base0(tau));
+    inv_pass<LOGN, Lay::B0, 0, 4, NP>(v, Lay::base0(tau), tw, p);
+}
+
+// Garner reconstruction of the signed integer with residues r0, r1, r2
+// (each in [0, p_i)), returned mod 2^64.  Valid for |x| < p0 p1 p2 / 2.
+__device__ __forceinline__ uint64_t crt3(uint32_t r0, uint32_t r1, uint32_t r2, const PrimeConsts &C)
+{
+    const uint32_t p0 = C.p[0], p1 = C.p[1], p2 = C.p[2];
+    // v1 = (r1 - r0) * p0^{-1} mod p1
+    const uint32_t r0m1 = csub(r0, p1);                    // r0 < p0 < 2 p1
+    const uint32_t v1 = csub(mul_shoup(C.c01, C.c01_sh, r1 + p1 - r0m1, p1), p1);
+    // v2 = (r2 - (r0 + p0 v1)) * (p0 p1)^{-1} mod p2
+    const uint32_t a = csub(mul_shoup(C.p0m2, C.p0m2_sh, v1, p2), p2);
+    const uint32_t b = csub(csub(r0, p2) + a, p2);
+    const uint32_t v2 = csub(mul_shoup(C.c012, C.c012_sh, r2 + p2 - b, p2), p2);
+    uint64_t x = (uint64_t)r0 + (uint64_t)p0 * v1 + C.p01 * (uint64_t)v2;
+    if (v2 > C.half2) x -= C.m64;
+    return x;
+}
+
+}  // namespace dev
+}  // namespace lvs

@@ -1,0 +1,590 @@
+// Wavefront scheduler and the server-side entry points.
+//
+// The cells of one anti-diagonal of the difference matrix are independent
+// (Section 6.2, "Parallelisation over cells"), and so are different string
+// pairs ("Batch inputs matching").  A batch therefore advances every pair one
+// anti-diagonal per launch step, and each step bootstraps the union of
+//   - the cell PBS of anti-diagonal d      (key of Eq. eq_keyeq2, LUT_min),
+//   - the second equality PBS of d+1       (Algorithm alg_ascii, LUT_EQ9),
+//   - the first equality PBS of d+2        (LUT_EQ)
+// over all pairs (two-lookup equality; with the one-lookup DNA equality the
+// pipeline is one step shorter).  Equality results live in two-slot rings
+// indexed by the parity of the anti-diagonal.
+//
+// Device memory of a batch ("arena"): rows of k*N+2 words (16-byte aligned
+// big LWE ciphertexts): string symbols, the frontier v[i] / h[j] and the rings.
+// It is allocated stream-ordered and released when the batch has been copied
+// into its result.
+#include <algorithm>
+#include <cstring>
+
+#include "lvs_internal.hpp"
+
+namespace lvs {
+
+namespace {
+
+struct Arena {
+    uint64_t *d = nullptr;
+    size_t stride = 0;
+    size_t rows = 0;
+    uint64_t *row(size_t r) const { return d + r * stride; }
+};
+
+lvs_status arena_alloc(lvs_ctx *ctx, size_t rows, Arena &A)
+{
+    A.stride = (size_t)ctx->P.big() + 2;
+    A.rows = rows;
+    if (rows == 0) return LVS_OK;
+    if (cudaMallocAsync((void **)&A.d, rows * A.stride * 8, ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(LVS_ERR_OOM, "device allocation of the batch arena failed (" +
+                                          std::to_string(rows * A.stride * 8 >> 20) + " MiB)");
+    }
+    return LVS_OK;
+}
+
+void arena_free(lvs_ctx *ctx, Arena &A)
+{
+    if (A.d) cudaFreeAsync(A.d, ctx->stream);
+    A.d = nullptr;
+}
+
+// host string -> consecutive arena rows
+lvs_status upload_string(lvs_ctx *ctx, const lvs_ct_string *s, const Arena &A, size_t first)
+{
+    const size_t nrows = s->len * s->symbols;
+    if (nrows == 0) return LVS_OK;
+    const size_t w = (size_t)s->big + 1;
+    LVS_CUDA(cudaMemcpy2DAsync(A.row(first), A.stride * 8, s->data.data(), w * 8, w * 8, nrows,
+                               cudaMemcpyHostToDevice, ctx->stream));
+    return LVS_OK;
+}
+
+Job make_job(const uint64_t *s0, int c0, const uint64_t *s1, int c1, const uint64_t *s2, int c2, int cst,
+             uint8_t lut, uint8_t kind, uint64_t *d0, uint64_t *d1)
+{
+    Job J;
+    memset(&J, 0, sizeof(J));
+    J.src[0] = s0; J.src[1] = s1; J.src[2] = s2;
+    J.coef[0] = (int8_t)c0; J.coef[1] = (int8_t)c1; J.coef[2] = (int8_t)c2;
+    J.cst = (int8_t)(((cst % 32) + 32) % 32);
+    J.lut = lut;
+    J.kind = kind;
+    J.dst[0] = d0; J.dst[1] = d1;
+    return J;
+}
+
+lvs_status make_result(lvs_ctx *ctx, size_t rows, lvs_result **out)
+{
+    lvs_result *r = new (std::nothrow) lvs_result;
+    if (!r) return set_error(LVS_ERR_OOM, "result allocation failed");
+    r->P = ctx->P;
+    r->device = ctx->device;
+    r->stride = (size_t)ctx->P.big() + 2;
+    if (rows && cudaMalloc((void **)&r->d, rows * r->stride * 8) != cudaSuccess) {
+        cudaGetLastError();
+        delete r;
+        return set_error(LVS_ERR_OOM, "device allocation of the result failed");
+    }
+    *out = r;
+    return LVS_OK;
+}
+
+lvs_status finish_result(lvs_ctx *ctx, lvs_result *r)
+{
+    LVS_CUDA(cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming));
+    LVS_CUDA(cudaEventRecord(r->done, ctx->stream));
+    return LVS_OK;
+}
+
+// Per pair plan: the rows of its strings, frontier and rings in the arena.
+struct PairRows {
+    size_t m = 0, n = 0;
+    uint32_t C = 2;          // equality lookups per cell (2 ASCII / 27, 1 DNA)
+    size_t x = 0, y = 0;     // first arena row of a / b (row = first + char * C + symbol)
+    const uint64_t *xd = nullptr, *yd = nullptr;   // device-resident strings (else arena rows)
+    size_t xs = 0, ys = 0;                         // their row strides
+    size_t v = 0, h = 0;     // v[i] at v + i - 1, h[j] at h + j - 1
+    size_t eq1 = 0, eq9 = 0; // ring rows: + (d & 1) * m + i - 1
+    const uint64_t *table = nullptr;   // preprocessed path: rows T[sym][i]
+    size_t table_stride = 0;
+    const int32_t *row_of = nullptr;
+    const uint8_t *plain = nullptr;
+};
+
+// cells (i, j) with i + j - 2 = d, 1 <= i <= m, 1 <= j <= n
+template <class F>
+void for_diag(const PairRows &P, long d, F f)
+{
+    if (d < 0 || P.m == 0 || P.n == 0) return;
+    const long lo = std::max<long>(1, d + 2 - (long)P.n), hi = std::min<long>((long)P.m, d + 1);
+    for (long i = lo; i <= hi; ++i) f((size_t)i, (size_t)(d + 2 - i));
+}
+
+void plan_pair_step(const PairRows &P, const Arena &A, long s, std::vector<Job> &jobs)
+{
+    auto X = [&](size_t i, int sym) {
+        return P.xd ? P.xd + ((i - 1) * P.C + sym) * P.xs : A.row(P.x + (i - 1) * P.C + sym);
+    };
+    auto Y = [&](size_t j, int sym) {
+        return P.yd ? P.yd + ((j - 1) * P.C + sym) * P.ys : A.row(P.y + (j - 1) * P.C + sym);
+    };
+    auto V = [&](size_t i) { return A.row(P.v + i - 1); };
+    auto H = [&](size_t j) { return A.row(P.h + j - 1); };
+    auto E1 = [&](long d, size_t i) { return A.row(P.eq1 + (size_t)(d & 1) * P.m + i - 1); };
+    auto E9 = [&](long d, size_t i) { return A.row(P.eq9 + (size_t)(d & 1) * P.m + i - 1); };
+    if (P.table) {
+        // preprocessed: EQ9[i][j] = T[b_j][i], one cell PBS per cell
+        for_diag(P, s, [&](size_t i, size_t j) {
+            const uint64_t *t = P.table + ((size_t)P.row_of[P.plain[j - 1]] * P.m + (i - 1)) * P.table_stride;
+            jobs.push_back(make_job(V(i), -1, H(j), 3, t, 1, 4, LUT_MIN, JOB_CELL, V(i), H(j)));
+        });
+        return;
+    }
+    if (P.C == 2) {
+        // EQ1 of diagonal s: z1 = x1_i - y1_j
+        for_diag(P, s, [&](size_t i, size_t j) {
+            jobs.push_back(make_job(X(i, 0), 1, Y(j, 0), -1, nullptr, 0, 0, LUT_EQ, JOB_STORE, E1(s, i), nullptr));
+        });
+        // EQ9 of diagonal s-1: z2 = 2 (x2_i - y2_j) + (1 - EQ1)
+        for_diag(P, s - 1, [&](size_t i, size_t j) {
+            jobs.push_back(make_job(X(i, 1), 2, Y(j, 1), -2, E1(s - 1, i), -1, 1, LUT_EQ9, JOB_STORE, E9(s - 1, i),
+                                    nullptr));
+        });
+        // cells of diagonal s-2: key = (1 - v[i][j-1]) + 3 (1 + h[i-1][j]) + EQ9
+        for_diag(P, s - 2, [&](size_t i, size_t j) {
+            jobs.push_back(make_job(V(i), -1, H(j), 3, E9(s - 2, i), 1, 4, LUT_MIN, JOB_CELL, V(i), H(j)));
+        });
+    } else {
+        // DNA: EQ9 = PBS(x_i - y_j; LUT_EQ9), one lookup
+        for_diag(P, s, [&](size_t i, size_t j) {
+            jobs.push_back(make_job(X(i, 0), 1, Y(j, 0), -1, nullptr, 0, 0, LUT_EQ9, JOB_STORE, E9(s, i), nullptr));
+        });
+        for_diag(P, s - 1, [&](size_t i, size_t j) {
+            jobs.push_back(make_job(V(i), -1, H(j), 3, E9(s - 1, i), 1, 4, LUT_MIN, JOB_CELL, V(i), H(j)));
+        });
+    }
+}
+
+// Runs the wavefront over all pairs; rows already placed.  Returns jobs count.
+lvs_status run_wavefront(lvs_ctx *ctx, const std::vector<PairRows> &pairs, const Arena &A, bool use_graph)
+{
+    long steps = 0;
+    for (const auto &P : pairs) {
+        if (P.m == 0 || P.n == 0) continue;
+        const long depth = P.table ? 0 : (long)P.C;
+        steps = std::max(steps, (long)(P.m + P.n - 2) + depth + 1);
+    }
+    std::vector<Job> jobs;
+    std::vector<size_t> off{0};
+    for (long s = 0; s < steps; ++s) {
+        for (const auto &P : pairs) plan_pair_step(P, A, s, jobs);
+        off.push_back(jobs.size());
+    }
+    return run_steps(ctx, jobs, off, use_graph);
+}
+
+lvs_status check_ctx_string(const lvs_ctx *ctx, const lvs_ct_string *s)
+{
+    if (!s) return set_error(LVS_ERR_ARG, "NULL encrypted string");
+    if (s->big != ctx->P.big()) return set_error(LVS_ERR_ARG, "encrypted string dimension does not match the context");
+    return LVS_OK;
+}
+
+}  // namespace
+}  // namespace lvs
+
+using namespace lvs;
+
+extern "C" {
+
+lvs_status lvs_edit_distance_batch(lvs_ctx *ctx, const lvs_ct_string *const *a, const lvs_ct_string *const *b,
+                                   size_t npairs, const lvs_opts *opts, lvs_result **out)
+{
+    if (!ctx || !out || (npairs && (!a || !b))) return set_error(LVS_ERR_ARG, "lvs_edit_distance_batch: NULL argument");
+    lvs_opts o;
+    lvs_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.band >= 0) return set_error(LVS_ERR_ARG, "lvs_edit_distance_batch: banded mode is not available");
+    std::vector<PairRows> pairs(npairs);
+    size_t rows = 0, xrows = 0, vrows = 0, hrows = 0, rrows = 0;
+    for (size_t p = 0; p < npairs; ++p) {
+        lvs_status st = check_ctx_string(ctx, a[p]);
+        if (st == LVS_OK) st = check_ctx_string(ctx, b[p]);
+        if (st != LVS_OK) return st;
+        if (symbols_per_char(a[p]->alphabet) != symbols_per_char(b[p]->alphabet) ||
+            (a[p]->alphabet == LVS_ALPHA_DNA4) != (b[p]->alphabet == LVS_ALPHA_DNA4))
+            return set_error(LVS_ERR_ARG, "lvs_edit_distance_batch: pair " + std::to_string(p) +
+                                              " mixes alphabets");
+        PairRows &P = pairs[p];
+        P.m = a[p]->len;
+        P.n = b[p]->len;
+        P.C = a[p]->symbols;
+        if (a[p]->d && a[p]->ddevice == ctx->device) { P.xd = a[p]->d; P.xs = a[p]->dstride; }
+        else xrows += P.m * P.C;
+        if (b[p]->d && b[p]->ddevice == ctx->device) { P.yd = b[p]->d; P.ys = b[p]->dstride; }
+        else xrows += P.n * P.C;
+        vrows += P.m;
+        hrows += P.n;
+        rrows += (P.C == 2 ? 4 : 2) * P.m;
+    }
+    // rows: [strings][v][h][rings]
+    rows = xrows + vrows + hrows + rrows;
+    LVS_CUDA(cudaSetDevice(ctx->device));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    Arena A;
+    lvs_status st = arena_alloc(ctx, rows, A);
+    if (st != LVS_OK) return st;
+    size_t cx = 0, cv = xrows, ch = xrows + vrows, cr = xrows + vrows + hrows;
+    for (size_t p = 0; p < npairs; ++p) {
+        PairRows &P = pairs[p];
+        if (!P.xd) { P.x = cx; cx += P.m * P.C; }
+        if (!P.yd) { P.y = cx; cx += P.n * P.C; }
+        P.v = cv; cv += P.m;
+        P.h = ch; ch += P.n;
+        if (P.C == 2) { P.eq1 = cr; cr += 2 * P.m; }
+        P.eq9 = cr; cr += 2 * P.m;
+        if ((!P.xd && (st = upload_string(ctx, a[p], A, P.x)) != LVS_OK) ||
+            (!P.yd && (st = upload_string(ctx, b[p], A, P.y)) != LVS_OK)) {
+            arena_free(ctx, A);
+            return st;
+        }
+    }
+    // OneMatrix boundary: v[i][0] = h[0][j] = 1 as noiseless ciphertexts (0, Delta)
+    cudaError_t e = launch_fill_trivial(A.d, A.stride, ctx->P.big(), xrows, vrows + hrows, 1ull << kDeltaLog,
+                                        ctx->stream);
+    if (e != cudaSuccess) { arena_free(ctx, A); return cuda_error(e, "fill"); }
+    ctx->launches += vrows + hrows ? 1 : 0;
+    st = run_wavefront(ctx, pairs, A, o.use_graph != 0);
+    if (st != LVS_OK) { arena_free(ctx, A); return st; }
+    lvs_result *r = nullptr;
+    st = make_result(ctx, hrows, &r);
+    if (st != LVS_OK) { arena_free(ctx, A); return st; }
+    size_t first = 0;
+    for (size_t p = 0; p < npairs; ++p) {
+        r->items.push_back({pairs[p].m, pairs[p].n, first, pairs[p].n});
+        first += pairs[p].n;
+    }
+    if (hrows) {
+        e = cudaMemcpy2DAsync(r->d, r->stride * 8, A.row(xrows + vrows), A.stride * 8, (ctx->P.big() + 1) * 8, hrows,
+                              cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e != cudaSuccess) { arena_free(ctx, A); lvs_result_free(r); return cuda_error(e, "result copy"); }
+    }
+    arena_free(ctx, A);
+    st = finish_result(ctx, r);
+    if (st != LVS_OK) { lvs_result_free(r); return st; }
+    *out = r;
+    return LVS_OK;
+}
+
+lvs_status lvs_eq(lvs_ctx *ctx, const lvs_ct_string *a, size_t i, const lvs_ct_string *b, size_t j, int times9,
+                  lvs_result **out)
+{
+    if (!ctx || !out) return set_error(LVS_ERR_ARG, "lvs_eq: NULL argument");
+    lvs_status st = check_ctx_string(ctx, a);
+    if (st == LVS_OK) st = check_ctx_string(ctx, b);
+    if (st != LVS_OK) return st;
+    if (i >= a->len || j >= b->len) return set_error(LVS_ERR_ARG, "lvs_eq: character index out of range");
+    if ((a->alphabet == LVS_ALPHA_DNA4) != (b->alphabet == LVS_ALPHA_DNA4))
+        return set_error(LVS_ERR_ARG, "lvs_eq: alphabets differ");
+    const uint32_t C = a->symbols;
+    LVS_CUDA(cudaSetDevice(ctx->device));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    Arena A;
+    // rows: x (C), y (C), eq1
+    if ((st = arena_alloc(ctx, 2 * C + 1, A)) != LVS_OK) return st;
+    const size_t w = (size_t)a->big + 1;
+    cudaError_t e = cudaMemcpy2DAsync(A.row(0), A.stride * 8, a->data.data() + i * C * w, w * 8, w * 8, C,
+                                      cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(A.row(C), A.stride * 8, b->data.data() + j * C * w, w * 8, w * 8, C,
+                              cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) { arena_free(ctx, A); return cuda_error(e, "lvs_eq upload"); }
+    lvs_result *r = nullptr;
+    if ((st = make_result(ctx, 1, &r)) != LVS_OK) { arena_free(ctx, A); return st; }
+    r->is_eq = true;
+    r->items.push_back({1, 1, 0, 1});
+    const uint8_t last = times9 ? LUT_EQ9 : LUT_EQ;
+    std::vector<Job> jobs;
+    std::vector<size_t> off{0};
+    if (C == 2) {
+        jobs.push_back(make_job(A.row(0), 1, A.row(C), -1, nullptr, 0, 0, LUT_EQ, JOB_STORE, A.row(2 * C), nullptr));
+        off.push_back(1);
+        jobs.push_back(make_job(A.row(1), 2, A.row(C + 1), -2, A.row(2 * C), -1, 1, last, JOB_STORE, r->d, nullptr));
+        off.push_back(2);
+    } else {
+        jobs.push_back(make_job(A.row(0), 1, A.row(C), -1, nullptr, 0, 0, last, JOB_STORE, r->d, nullptr));
+        off.push_back(1);
+    }
+    st = run_steps(ctx, jobs, off, false);
+    arena_free(ctx, A);
+    if (st == LVS_OK) st = finish_result(ctx, r);
+    if (st != LVS_OK) { lvs_result_free(r); return st; }
+    *out = r;
+    return LVS_OK;
+}
+
+lvs_status lvs_preprocess(lvs_ctx *ctx, const lvs_ct_string *enc, const uint8_t *subset, size_t nsub,
+                          lvs_eq_table **out)
+{
+    if (!ctx || !out) return set_error(LVS_ERR_ARG, "lvs_preprocess: NULL argument");
+    lvs_status st = check_ctx_string(ctx, enc);
+    if (st != LVS_OK) return st;
+    std::vector<uint8_t> sub;
+    if (subset) sub.assign(subset, subset + nsub);
+    else
+        for (uint32_t s = 0; s < alphabet_size(enc->alphabet); ++s) sub.push_back(alphabet_char(enc->alphabet, s));
+    lvs_eq_table *t = new (std::nothrow) lvs_eq_table;
+    if (!t) return set_error(LVS_ERR_OOM, "lvs_preprocess: host allocation failed");
+    t->P = ctx->P;
+    t->device = ctx->device;
+    t->alphabet = enc->alphabet;
+    t->len = enc->len;
+    t->stride = (size_t)ctx->P.big() + 2;
+    for (int c = 0; c < 256; ++c) t->row_of[c] = -1;
+    std::vector<std::pair<uint32_t, uint32_t>> sym(sub.size());
+    for (size_t r = 0; r < sub.size(); ++r) {
+        uint32_t v[2] = {0, 0};
+        if (!encode_char(enc->alphabet, sub[r], v) || t->row_of[sub[r]] >= 0) {
+            delete t;
+            return set_error(LVS_ERR_ARG, "lvs_preprocess: subset character " + std::to_string(sub[r]) +
+                                              " is outside the alphabet or repeated");
+        }
+        t->row_of[sub[r]] = (int32_t)r;
+        sym[r] = {v[0], v[1]};
+    }
+    t->subset = sub;
+    const size_t m = enc->len, C = enc->symbols, R = sub.size();
+    LVS_CUDA(cudaSetDevice(ctx->device));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (R * m && cudaMalloc((void **)&t->d, R * m * t->stride * 8) != cudaSuccess) {
+        cudaGetLastError();
+        delete t;
+        return set_error(LVS_ERR_OOM, "lvs_preprocess: device allocation of the table failed");
+    }
+    Arena A;   // rows: x (m*C), eq1 (R*m)
+    if ((st = arena_alloc(ctx, m * C + (C == 2 ? R * m : 0), A)) != LVS_OK) { lvs_eq_table_free(t); return st; }
+    if ((st = upload_string(ctx, enc, A, 0)) != LVS_OK) { arena_free(ctx, A); lvs_eq_table_free(t); return st; }
+    std::vector<Job> jobs;
+    std::vector<size_t> off{0};
+    auto T = [&](size_t r, size_t i) { return t->d + (r * m + i) * t->stride; };
+    if (C == 2) {
+        // EQ1 = PBS(x1_i - sigma1; LUT_EQ), EQ9 = PBS(2 (x2_i - sigma2) + 1 - EQ1; LUT_EQ9)
+        for (size_t r = 0; r < R; ++r)
+            for (size_t i = 0; i < m; ++i)
+                jobs.push_back(make_job(A.row(i * C), 1, nullptr, 0, nullptr, 0, -(int)sym[r].first, LUT_EQ, JOB_STORE,
+                                        A.row(m * C + r * m + i), nullptr));
+        off.push_back(jobs.size());
+        for (size_t r = 0; r < R; ++r)
+            for (size_t i = 0; i < m; ++i)
+                jobs.push_back(make_job(A.row(i * C + 1), 2, A.row(m * C + r * m + i), -1, nullptr, 0,
+                                        1 - 2 * (int)sym[r].second, LUT_EQ9, JOB_STORE, T(r, i), nullptr));
+        off.push_back(jobs.size());
+    } else {
+        for (size_t r = 0; r < R; ++r)
+            for (size_t i = 0; i < m; ++i)
+                jobs.push_back(make_job(A.row(i), 1, nullptr, 0, nullptr, 0, -(int)sym[r].first, LUT_EQ9, JOB_STORE,
+                                        T(r, i), nullptr));
+        off.push_back(jobs.size());
+    }
+    st = run_steps(ctx, jobs, off, false);
+    arena_free(ctx, A);
+    if (st == LVS_OK) {
+        if (cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(t->done, ctx->stream) != cudaSuccess)
+            st = set_error(LVS_ERR_CUDA, "lvs_preprocess: event");
+    }
+    if (st != LVS_OK) { lvs_eq_table_free(t); return st; }
+    *out = t;
+    return LVS_OK;
+}
+
+void lvs_eq_table_free(lvs_eq_table *t)
+{
+    if (!t) return;
+    cudaSetDevice(t->device);
+    if (t->done) { cudaEventSynchronize(t->done); cudaEventDestroy(t->done); }
+    if (t->d) cudaFree(t->d);
+    cudaGetLastError();
+    delete t;
+}
+
+lvs_status lvs_edit_distance_preprocessed_batch(lvs_ctx *ctx, const lvs_eq_table *const *t, const uint8_t *const *plain,
+                                                const size_t *plain_len, size_t nq, const lvs_opts *opts,
+                                                lvs_result **out)
+{
+    if (!ctx || !out || (nq && (!t || !plain || !plain_len)))
+        return set_error(LVS_ERR_ARG, "lvs_edit_distance_preprocessed_batch: NULL argument");
+    lvs_opts o;
+    lvs_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.band >= 0) return set_error(LVS_ERR_ARG, "banded mode is not available");
+    std::vector<PairRows> pairs(nq);
+    size_t vrows = 0, hrows = 0;
+    for (size_t q = 0; q < nq; ++q) {
+        if (!t[q] || (plain_len[q] && !plain[q])) return set_error(LVS_ERR_ARG, "NULL table or string");
+        if (t[q]->P.p.N != ctx->P.p.N || t[q]->device != ctx->device)
+            return set_error(LVS_ERR_ARG, "table does not belong to this context");
+        for (size_t j = 0; j < plain_len[q]; ++j)
+            if (t[q]->row_of[plain[q][j]] < 0)
+                return set_error(LVS_ERR_ARG, "query " + std::to_string(q) + ": plaintext character " +
+                                                  std::to_string(plain[q][j]) + " is not in the table subset");
+        PairRows &P = pairs[q];
+        P.m = t[q]->len;
+        P.n = plain_len[q];
+        P.table = t[q]->d;
+        P.table_stride = t[q]->stride;
+        P.row_of = t[q]->row_of;
+        P.plain = plain[q];
+        vrows += P.m;
+        hrows += P.n;
+    }
+    LVS_CUDA(cudaSetDevice(ctx->device));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    for (size_t q = 0; q < nq; ++q)
+        if (t[q]->done) LVS_CUDA(cudaStreamWaitEvent(ctx->stream, t[q]->done, 0));
+    Arena A;
+    lvs_status st = arena_alloc(ctx, vrows + hrows, A);
+    if (st != LVS_OK) return st;
+    size_t cv = 0, ch = vrows;
+    for (auto &P : pairs) {
+        P.v = cv; cv += P.m;
+        P.h = ch; ch += P.n;
+    }
+    cudaError_t e = launch_fill_trivial(A.d, A.stride, ctx->P.big(), 0, vrows + hrows, 1ull << kDeltaLog, ctx->stream);
+    if (e != cudaSuccess) { arena_free(ctx, A); return cuda_error(e, "fill"); }
+    ctx->launches += vrows + hrows ? 1 : 0;
+    st = run_wavefront(ctx, pairs, A, o.use_graph != 0);
+    if (st != LVS_OK) { arena_free(ctx, A); return st; }
+    lvs_result *r = nullptr;
+    if ((st = make_result(ctx, hrows, &r)) != LVS_OK) { arena_free(ctx, A); return st; }
+    size_t first = 0;
+    for (auto &P : pairs) { r->items.push_back({P.m, P.n, first, P.n}); first += P.n; }
+    if (hrows) {
+        e = cudaMemcpy2DAsync(r->d, r->stride * 8, A.row(vrows), A.stride * 8, (ctx->P.big() + 1) * 8, hrows,
+                              cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e != cudaSuccess) { arena_free(ctx, A); lvs_result_free(r); return cuda_error(e, "result copy"); }
+    }
+    arena_free(ctx, A);
+    if ((st = finish_result(ctx, r)) != LVS_OK) { lvs_result_free(r); return st; }
+    *out = r;
+    return LVS_OK;
+}
+
+lvs_status lvs_ct_string_upload(lvs_ctx *ctx, lvs_ct_string *s)
+{
+    if (!ctx || !s) return set_error(LVS_ERR_ARG, "lvs_ct_string_upload: NULL argument");
+    lvs_status st = check_ctx_string(ctx, s);
+    if (st != LVS_OK) return st;
+    if (s->d && s->ddevice == ctx->device) return LVS_OK;
+    if (s->d) return set_error(LVS_ERR_STATE, "lvs_ct_string_upload: string already resident on another device");
+    const size_t rows = s->len * s->symbols;
+    if (rows == 0) return LVS_OK;
+    LVS_CUDA(cudaSetDevice(ctx->device));
+    const size_t stride = (size_t)s->big + 2, w = (size_t)s->big + 1;
+    uint64_t *d = nullptr;
+    if (cudaMalloc((void **)&d, rows * stride * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(LVS_ERR_OOM, "lvs_ct_string_upload: device allocation failed");
+    }
+    cudaError_t e = cudaMemcpy2D(d, stride * 8, s->data.data(), w * 8, w * 8, rows, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(d); return cuda_error(e, "lvs_ct_string_upload"); }
+    s->d = d;
+    s->dstride = stride;
+    s->ddevice = ctx->device;
+    return LVS_OK;
+}
+
+lvs_status lvs_result_info(const lvs_result *r, size_t *items, size_t pair, size_t *m, size_t *n)
+{
+    if (!r) return set_error(LVS_ERR_ARG, "lvs_result_info: NULL result");
+    if (items) *items = r->items.size();
+    if (m || n) {
+        if (pair >= r->items.size()) return set_error(LVS_ERR_ARG, "lvs_result_info: item out of range");
+        if (m) *m = r->items[pair].m;
+        if (n) *n = r->items[pair].n;
+    }
+    return LVS_OK;
+}
+
+lvs_status lvs_result_export(const lvs_result *r, size_t pair, uint64_t *dst, size_t *words)
+{
+    if (!r || !words) return set_error(LVS_ERR_ARG, "lvs_result_export: NULL argument");
+    if (pair >= r->items.size()) return set_error(LVS_ERR_ARG, "lvs_result_export: item out of range");
+    const auto &it = r->items[pair];
+    const size_t w = (size_t)r->P.big() + 1;
+    if (dst) {
+        if (*words < it.count * w) return set_error(LVS_ERR_ARG, "lvs_result_export: destination too small");
+        LVS_CUDA(cudaSetDevice(r->device));
+        LVS_CUDA(cudaEventSynchronize(r->done));
+        if (it.count)
+            LVS_CUDA(cudaMemcpy2D(dst, w * 8, r->d + it.first * r->stride, r->stride * 8, w * 8, it.count,
+                                  cudaMemcpyDeviceToHost));
+    }
+    *words = it.count * w;
+    return LVS_OK;
+}
+
+void lvs_result_free(lvs_result *r)
+{
+    if (!r) return;
+    cudaSetDevice(r->device);
+    if (r->done) { cudaEventSynchronize(r->done); cudaEventDestroy(r->done); }
+    if (r->d) cudaFree(r->d);
+    cudaGetLastError();
+    delete r;
+}
+
+static lvs_status decrypt_rows(const lvs_client_key *ck, const lvs_result *r, const uint64_t *host, size_t pair,
+                               uint32_t *out)
+{
+    const auto &it = r->items[pair];
+    const size_t w = (size_t)r->P.big() + 1;
+    if (r->is_eq) {
+        *out = decrypt_lwe(*ck, host);
+        return LVS_OK;
+    }
+    // D[m][n] = m + sum_{j=1..n} h[m][j], each h in {-1, 0, 1} (Z_32 residues)
+    long d = (long)it.m;
+    for (size_t j = 0; j < it.count; ++j) {
+        const uint32_t v = decrypt_lwe(*ck, host + j * w);
+        d += v >= 16 ? (long)v - 32 : (long)v;
+    }
+    *out = (uint32_t)std::max(0L, d);
+    return LVS_OK;
+}
+
+lvs_status lvs_decrypt(const lvs_client_key *ck, const lvs_result *r, size_t pair, uint32_t *dist)
+{
+    if (!ck || !r || !dist) return set_error(LVS_ERR_ARG, "lvs_decrypt: NULL argument");
+    if (pair >= r->items.size()) return set_error(LVS_ERR_ARG, "lvs_decrypt: item out of range");
+    if (ck->P.big() != r->P.big()) return set_error(LVS_ERR_ARG, "lvs_decrypt: key does not match the result");
+    size_t words = 0;
+    lvs_status st = lvs_result_export(r, pair, nullptr, &words);
+    if (st != LVS_OK) return st;
+    std::vector<uint64_t> host(words);
+    if ((st = lvs_result_export(r, pair, host.data(), &words)) != LVS_OK) return st;
+    return decrypt_rows(ck, r, host.data(), pair, dist);
+}
+
+lvs_status lvs_decrypt_all(const lvs_client_key *ck, const lvs_result *r, uint32_t *dist)
+{
+    if (!ck || !r || (!dist && !r->items.empty())) return set_error(LVS_ERR_ARG, "lvs_decrypt_all: NULL argument");
+    if (r->items.empty()) return LVS_OK;
+    const size_t w = (size_t)r->P.big() + 1;
+    size_t total = 0;
+    for (const auto &it : r->items) total = std::max(total, it.first + it.count);
+    std::vector<uint64_t> host(total * w);
+    LVS_CUDA(cudaSetDevice(r->device));
+    LVS_CUDA(cudaEventSynchronize(r->done));
+    if (total)
+        LVS_CUDA(cudaMemcpy2D(host.data(), w * 8, r->d, r->stride * 8, w * 8, total, cudaMemcpyDeviceToHost));
+    for (size_t p = 0; p < r->items.size(); ++p) {
+        lvs_status st = decrypt_rows(ck, r, host.data() + r->items[p].first * w, p, dist + p);
+        if (st != LVS_OK) return st;
+    }
+    return LVS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+"""The C-ABI library: builds, loads without a GPU, exports every symbol that
+include/lvs.h declares, and its host-side logic (key generation, encryption,
+decryption, argument checks) matches the oracle -- no GPU needed."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import plain as P
+from oracle import tfhe as T
+from paper_2508_14568_gb300 import lvs as L
+from tests.conftest import ROOT
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lvs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(lvs_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = L.lib()
+    declared = declared_functions()
+    assert len(declared) >= 30
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(L.EXPORTS) == declared
+
+
+def test_version_and_params():
+    assert "sm_103a" in L.lvs_version()
+    p = L.lvs_params_default()
+    q = T.params_lvs()
+    assert p.as_dict() == q.as_dict()
+    assert L.lvs_params_test().as_dict() == T.params_test().as_dict()
+
+
+def test_keygen_matches_oracle_bit_for_bit_test_params():
+    p = L.lvs_params_test()
+    ck, sk = L.lvs_keygen(p, 0)
+    K = T.Keys(T.params_test(), 0)
+    lwe, glwe = L.lvs_client_key_export(ck)
+    bsk, ksk = L.lvs_server_key_export(sk)
+    assert np.array_equal(lwe, K.lwe_key)
+    assert np.array_equal(glwe, K.glwe_key)
+    assert np.array_equal(bsk, K.bsk)
+    assert np.array_equal(ksk, K.ksk)
+
+
+@pytest.mark.slow
+def test_keygen_matches_oracle_full_params():
+    p = L.lvs_params_default()
+    ck, sk = L.lvs_keygen(p, 0)
+    K = T.Keys(T.params_lvs(), 0)
+    lwe, glwe = L.lvs_client_key_export(ck)
+    bsk, ksk = L.lvs_server_key_export(sk)
+    assert np.array_equal(lwe, K.lwe_key) and np.array_equal(glwe, K.glwe_key)
+    assert np.array_equal(ksk, K.ksk)
+    assert np.array_equal(bsk, K.bsk)
+
+
+def test_encrypt_string_matches_oracle():
+    p = L.lvs_params_test()
+    ck, sk = L.lvs_keygen(p, 3)
+    K = T.Keys(T.params_test(), 3)
+    for alpha, la, s in [(L.LVS_ALPHA_ASCII7, P.ALPHA_ASCII7, "Hi, there~"),
+                         (L.LVS_ALPHA_27, P.ALPHA_27, "AB Z"),
+                         (L.LVS_ALPHA_DNA4, P.ALPHA_DNA4, "GATTACA")]:
+        cs = L.lvs_encrypt_string(ck, s, alpha, 77, 5)
+        got = L.lvs_ct_string_export(cs)
+        want = T.encrypt_string(K, s, la, 77, 5)
+        assert got.shape[0] == len(s)
+        for i in range(len(s)):
+            for t in range(got.shape[1]):
+                assert np.array_equal(got[i, t], want[i][t])
+                assert L.lvs_decrypt_lwe(ck, got[i, t]) == T.decrypt(K, want[i][t])
+
+
+def test_encrypt_lwe_and_decrypt():
+    ck, _ = L.lvs_keygen(L.lvs_params_test(), 4)
+    K = T.Keys(T.params_test(), 4)
+    for v in range(32):
+        ct = L.lvs_encrypt_lwe(ck, v, 9, 1, v, 512)
+        assert np.array_equal(ct, T.encrypt(K, v, 9, 1, v))
+        assert L.lvs_decrypt_lwe(ck, ct) == v
+
+
+def test_argument_errors_are_reported():
+    p = L.lvs_params_test()
+    bad = L.lvs_params()
+    ctypes.memmove(ctypes.byref(bad), ctypes.byref(p), ctypes.sizeof(p))
+    bad.N = 1000
+    with pytest.raises(L.LvsError) as e:
+        L.lvs_keygen(bad, 0)
+    assert e.value.status == L.LVS_ERR_ARG
+    ck, _ = L.lvs_keygen(p, 0)
+    with pytest.raises(L.LvsError) as e:
+        L.lvs_encrypt_string(ck, "abc", L.LVS_ALPHA_27, 0, 0)      # lowercase not in alphabet
+    assert e.value.status == L.LVS_ERR_ARG
+    with pytest.raises(L.LvsError) as e:
+        L.lvs_encrypt_string(ck, "ACGU", L.LVS_ALPHA_DNA4, 0, 0)
+    assert e.value.status == L.LVS_ERR_ARG
+    # empty strings are valid
+    s = L.lvs_encrypt_string(ck, "", L.LVS_ALPHA_ASCII7, 0, 0)
+    assert L.lvs_ct_string_info(s)["len"] == 0
+
+
+def test_ct_string_import_roundtrip():
+    ck, _ = L.lvs_keygen(L.lvs_params_test(), 1)
+    s = L.lvs_encrypt_string(ck, "KID", L.LVS_ALPHA_ASCII7, 2, 0)
+    arr = L.lvs_ct_string_export(s)
+    s2 = L.lvs_ct_string_import(arr, L.LVS_ALPHA_ASCII7)
+    assert np.array_equal(L.lvs_ct_string_export(s2), arr)
+
+
+def test_context_without_gpu_fails_loudly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    _, sk = L.lvs_keygen(L.lvs_params_test(), 0)
+    with pytest.raises(L.LvsError) as e:
+        L.lvs_ctx_create(sk, 0)
+    assert e.value.status == L.LVS_ERR_CUDA
