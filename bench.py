@@ -1,0 +1,437 @@
+#!/usr/bin/env python3
+"""Benchmark of the encrypted Leuvenshtein hot path on GB300.
+
+Default workload (one "step"): the batching configuration -- 256 encrypted
+ASCII pairs, lengths uniform in [8, 16], 30% near-duplicates -- under the full
+TFHE parameter set (n=834, N=2048), all pairs advanced together in
+anti-diagonal-union launches (3 PBS per cell).  Metric: encrypted DP cells/s
+(whole job, all GPUs); PBS/s and the roofline fraction of the blind-rotation
+kernel ride along.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lvs|reference]
+                  [--config 1|2|3|4] [--pairs P] [--no-e2e] [--no-cpu-baseline]
+
+N > 1 is launched with torch.distributed.run (one rank per GPU): every rank
+runs its own batch of independent pairs (weak scaling, no data-path
+collective); timing is max over ranks.  --impl reference times the CPU oracle
+(oracle/, schoolbook TFHE) on the host cores on a bounded sample of the same
+workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SM_COUNT_NOMINAL = 152
+MUL32_PER_SM_CLK = 64        # 32-bit integer multiply throughput per SM per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lvs", choices=["lvs", "reference"])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--pairs", type=int, default=None, help="override the number of pairs (small profiling cases)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=None, help="PBS in the oracle sample (default: host cores)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- workloads
+
+def workload(cfg, rank, pairs_override):
+    from paper_2508_14568_gb300 import workloads as W
+    if cfg == 1:
+        pairs = W.config1(W.SEED_BASE + 1 + 100 * rank)
+        alpha, desc = "ascii7", "config 1: one encrypted ASCII pair, lengths 4 and 4"
+    elif cfg == 2:
+        pairs = W.config2(W.SEED_BASE + 2 + 100 * rank, pairs=pairs_override or 256)
+        alpha = "ascii7"
+        desc = "config 2: %d encrypted ASCII pairs, lengths U[8,16], 30%% near-duplicates" % len(pairs)
+    elif cfg == 3:
+        pairs = W.config3(W.SEED_BASE + 3 + 100 * rank, queries=pairs_override or 1024)
+        alpha = "alpha27"
+        desc = "config 3: %d preprocessed queries, 27 symbols, lengths U[8,32]" % len(pairs)
+    else:
+        pairs = W.config4(W.SEED_BASE + 4 + 100 * rank, pairs=pairs_override or 64)
+        alpha = "dna4"
+        desc = "config 4: %d encrypted DNA pairs, lengths U[64,256], 10%% mutation" % len(pairs)
+    return pairs, alpha, desc
+
+
+def pbs_per_cell(cfg):
+    return {1: 3, 2: 3, 3: 1, 4: 2}[cfg]
+
+
+def modmul_per_pbs(p):
+    """Algorithmic modular multiplications of one blind rotation on the exact
+    NTT path: n * P * [((k+1) l + (k+1)) (N/2) log2 N + (k+1)^2 l N]
+    (forward transforms of the digit polynomials, inverse transforms of the
+    outputs, pointwise key products), P = 3 primes."""
+    logN = p.N.bit_length() - 1
+    k, l = p.k, p.pbs_level
+    return p.n * 3 * (((k + 1) * l + (k + 1)) * (p.N // 2) * logN + (k + 1) ** 2 * l * p.N)
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+
+def oracle_sample(pairs, alpha, count, seed=0):
+    """`count` PBS inputs of the workload (first-equality inputs x1_i - y1_j of
+    successive cells, LUT_EQ; all PBS of the method cost the same), built by the
+    oracle itself from its own keys and encryption."""
+    import numpy as np
+    from oracle import plain as P
+    from oracle import tfhe as T
+    K = T.Keys(T.params_lvs(), seed)
+    cts, luts = [], []
+    k = 0
+    for pi, (a, b) in enumerate(pairs):
+        xa = T.encrypt_string(K, a[:4], alpha, 99, 2 * pi)
+        yb = T.encrypt_string(K, b[:4], alpha, 99, 2 * pi + 1)
+        for i in range(len(xa)):
+            for j in range(len(yb)):
+                if k < count:
+                    cts.append(xa[i][0] - yb[j][0])
+                    luts.append(P.LUT_EQ)
+                    k += 1
+        if k >= count:
+            break
+    return K, np.stack(cts), np.asarray(luts, np.uint32)
+
+
+def time_oracle(K, cts, luts, cores):
+    from oracle import tfhe as T
+    t0 = time.perf_counter()
+    out = T.pbs_many(K, cts, luts, nthreads=cores)
+    return time.perf_counter() - t0, out
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import tfhe as T
+    cfg = args.config
+    pairs, alpha, desc = workload(cfg, 0, args.pairs)
+    cores = os.cpu_count() or 1
+    count = args.cpu_sample or cores
+    T.build()
+    K, cts, luts = oracle_sample(pairs, alpha, count)
+    for _ in range(args.warmup):
+        time_oracle(K, cts[:min(len(cts), cores)], luts[:min(len(cts), cores)], cores)
+    total = 0.0
+    for _ in range(args.steps):
+        dt, _ = time_oracle(K, cts, luts, cores)
+        total += dt
+    pbs_s = count * args.steps / total
+    cells_s = pbs_s / pbs_per_cell(cfg)
+    sample = "%d independent full-parameter PBS per step (schoolbook TFHE, %d threads); cells/s = PBS/s / %d" % (
+        count, cores, pbs_per_cell(cfg))
+    line = {
+        "impl": "reference", "metric": "encrypted DP cells/s", "value": cells_s, "unit": "cells/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": desc, "params": "n=834 k=1 N=2048 pbs 2x2^13 ks 5x2^3"},
+        "pbs_per_s": pbs_s,
+        "cpu_baseline": {"value": cells_s, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": cells_s, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "ntt.cuh"):
+        with open(os.path.join(ROOT, "paper_2508_14568_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record():
+    """DRAM bytes per blind-rotation launch from the committed ncu summary, if
+    it was taken on the current kernel source (else null)."""
+    path = os.path.join(ROOT, "profiles", "br_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    if rec.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return rec
+
+
+def run_lvs(args):
+    import torch
+    import torch.distributed as dist
+    from oracle import plain as P  # WF for the distance check only (plaintext)
+    from paper_2508_14568_gb300 import lvs as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    cfg = args.config
+    pairs, alpha, desc = workload(cfg, rank, args.pairs)
+    A_L = {"ascii7": L.LVS_ALPHA_ASCII7, "alpha27": L.LVS_ALPHA_27, "dna4": L.LVS_ALPHA_DNA4}[alpha]
+    params = L.lvs_params_default()
+    ck, sk = L.lvs_keygen(params, 0)
+    stream = torch.cuda.current_stream()
+    ctx = L.lvs_ctx_create(sk, local, stream)
+    big = params.k * params.N
+    cells = sum(len(a) * len(b) for a, b in pairs)
+    want = [P.wf_distance(a, b) for a, b in pairs]
+
+    def encrypt_all(seed):
+        if cfg == 3:
+            return [L.lvs_encrypt_string(ck, a, A_L, seed, k) for k, (a, b) in enumerate(pairs)], None
+        A = [L.lvs_encrypt_string(ck, a, A_L, seed, 2 * k) for k, (a, b) in enumerate(pairs)]
+        B = [L.lvs_encrypt_string(ck, b, A_L, seed, 2 * k + 1) for k, (a, b) in enumerate(pairs)]
+        return A, B
+
+    # device-resident inputs for the kernel-side number
+    A_dev, B_dev = encrypt_all(7)
+    tables = None
+    if cfg == 3:
+        tables = [L.lvs_preprocess(ctx, s) for s in A_dev]   # offline phase, not timed
+        plains = [b for a, b in pairs]
+        step = lambda: L.lvs_edit_distance_preprocessed_batch(ctx, tables, plains)
+    else:
+        for s in A_dev + B_dev:
+            L.lvs_ct_string_upload(ctx, s)
+        step = lambda: L.lvs_edit_distance_batch(ctx, A_dev, B_dev)
+
+    # warm-up (+ correctness of every distance)
+    r = None
+    for w in range(max(1, args.warmup)):
+        r = step()
+        if w == 0:
+            got = L.lvs_decrypt_all(ck, r)
+            assert got == want, "decrypted distances differ from Wagner-Fischer"
+    torch.cuda.synchronize()
+    r = None
+
+    L.lvs_ctx_set_timing(ctx, True)
+    launches0 = L.lvs_ctx_launch_count(ctx)
+    pbs0 = L.lvs_ctx_pbs_count(ctx)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        r = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    r = None
+    dev_ms = ev0.elapsed_time(ev1)
+    launches = L.lvs_ctx_launch_count(ctx) - launches0
+    pbs_done = L.lvs_ctx_pbs_count(ctx) - pbs0
+    br = L.lvs_ctx_kernel_stats(ctx, 0)
+    ks = L.lvs_ctx_kernel_stats(ctx, 1)
+    L.lvs_ctx_set_timing(ctx, False)
+
+    t_max = max_over_ranks(dev_ms / 1e3)
+    cells_all = sum_over_ranks(cells * args.steps)
+    pbs_all = sum_over_ranks(pbs_done)
+    value = cells_all / t_max
+
+    # roofline of the blind-rotation kernel (ALU bound: 32-bit multiplies)
+    w_mod = modmul_per_pbs(params)
+    avg_launch_s = br["total_ms"] / max(1, br["launches"]) / 1e3
+    units_per_launch = br["items"] / max(1, br["launches"])
+    achieved = 3 * w_mod * units_per_launch / avg_launch_s / 1e12 if br["launches"] else None
+    sm_mhz_max = clk.get("sm_max_mhz") or 2070.0
+    peak = SM_COUNT_NOMINAL * MUL32_PER_SM_CLK * sm_mhz_max * 1e6 / 1e12
+    trec = traffic_record()
+    traffic = None
+    if trec:
+        traffic = trec["dram_bytes_per_pbs"] * units_per_launch
+
+    # end to end: host strings in, decrypted distances out
+    e2e = None
+    if not args.no_e2e:
+        A_h, B_h = encrypt_all(11)
+        if cfg == 3:
+            e2e_step = lambda: L.lvs_edit_distance_preprocessed_batch(ctx, tables, plains)
+            h2d = 0
+        else:
+            e2e_step = lambda: L.lvs_edit_distance_batch(ctx, A_h, B_h)
+            h2d = sum((len(a) + len(b)) * (2 if cfg != 4 else 1) * (big + 1) * 8 for a, b in pairs)
+        d2h = sum(len(b) * (big + 1) * 8 for a, b in pairs)
+        got = L.lvs_decrypt_all(ck, e2e_step())
+        assert got == want
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            got = L.lvs_decrypt_all(ck, e2e_step())
+        torch.cuda.synchronize()
+        barrier()
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": cells_all / t_e2e, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": 1e3 * t_e2e / args.steps,
+               "note": "host encrypted strings -> lvs_edit_distance_batch -> D2H + client decryption"}
+
+    # CPU oracle baseline (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import numpy as np
+        cores = os.cpu_count() or 1
+        count = args.cpu_sample or cores
+        K, cts, luts = oracle_sample(pairs, alpha, count)
+        dt, out = time_oracle(K, cts, luts, cores)
+        # the same inputs through the GPU PBS (parity of the sample)
+        d_in = torch.from_numpy(np.ascontiguousarray(cts).view(np.int64)).cuda()
+        d_lut = torch.from_numpy(np.ascontiguousarray(luts.astype(np.uint8))).cuda()
+        d_out = torch.zeros_like(d_in)
+        # the oracle keys equal the library keys from the same seed
+        L.lvs_pbs_batch_device(ctx, d_in, big + 1, d_lut, d_out, big + 1, count)
+        L.lvs_ctx_synchronize(ctx)
+        same = bool(np.array_equal(d_out.cpu().numpy().view(np.uint64), out))
+        pbs_s = count / dt
+        cpu = {"value": pbs_s / pbs_per_cell(cfg), "unit": "cells/s", "cores": cores, "kind": "oracle",
+               "sample": "%d full-parameter PBS of the workload on %d threads (%.1f s); cells/s = PBS/s / %d"
+                         % (count, cores, dt, pbs_per_cell(cfg)),
+               "pbs_per_s": pbs_s, "sample_bit_exact_vs_gpu": same}
+
+    if rank == 0:
+        line = {
+            "metric": "encrypted DP cells/s",
+            "value": value,
+            "unit": "cells/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": t_max * 1e3 / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": desc, "pairs_per_gpu": len(pairs), "cells_per_gpu_step": cells,
+                       "pbs_per_gpu_step": pbs_done // max(1, args.steps),
+                       "params": "n=834 k=1 N=2048 pbs 2x2^13 ks 5x2^3 (TUniform 2^45 / 2^17)",
+                       "l2": "inputs larger than L2 (server key 232 MB on device)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "pbs_per_s": pbs_all / t_max,
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul32/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                         "kernel": "k_blind_rotate<11>",
+                         "units_per_launch": units_per_launch, "launch_ms": avg_launch_s * 1e3,
+                         "mul32_per_pbs": 3 * w_mod,
+                         "peak_note": "%d SMs x %d int32 mul/clk x max SM clock (derived)" % (
+                             SM_COUNT_NOMINAL, MUL32_PER_SM_CLK)},
+            "kernels": {"blind_rotate": br, "keyswitch": ks},
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_lvs(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

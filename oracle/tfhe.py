@@ -219,7 +219,7 @@ def trivial(keys, mu_z32):
 
 def add_const(ct, mu_z32):
     out = ct.copy()
-    out[-1] = out[-1] + U64((int(mu_z32) % 32) * DELTA)
+    out[-1] = U64((int(out[-1]) + (int(mu_z32) % 32) * DELTA) % 2**64)
     return out
 
 
