@@ -227,6 +227,30 @@ lvs_status lvs_pbs_batch_device(lvs_ctx *ctx, const uint64_t *d_in, size_t in_st
                                 const uint8_t *d_lut, uint64_t *d_out, size_t out_stride,
                                 size_t count);
 
+/* Allocation-free variant of lvs_pbs_batch_device (the paper has no
+ * counterpart; this is a service of the library).  For callers that cannot
+ * allocate device memory while they run -- a server that reserves its whole
+ * memory budget at start-up and must not fail mid-request, a latency-critical
+ * path that cannot take cudaMalloc's implicit synchronisation, or a host
+ * program whose device allocator belongs to another framework.  Same
+ * arguments, same result bit for bit; it calls no cudaMalloc / cudaFree and no
+ * allocating routine on its success path.  Its scratch (job descriptors and
+ * the modulus-switched masks passed from the key-switch kernel to the
+ * blind-rotation kernel) lives in one static device array of
+ * LVS_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits.  Limit: count * (48 + 4 (n+1)) bytes + 256 must fit, i.e. at
+ * most 1237 PBS per call for n = 834 (13617 for n = 64); larger counts fail
+ * with LVS_ERR_ARG and do nothing.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the one array and every call rewrites
+ * the part it uses before reading it (nothing needs to start at zero): calls
+ * that overlap on the GPU -- different streams or contexts of the same device
+ * -- race on it; issue them on one stream or serialise them. */
+#define LVS_NOALLOC_SCRATCH_BYTES (4u << 20)
+lvs_status lvs_pbs_batch_device_noalloc(lvs_ctx *ctx, const uint64_t *d_in, size_t in_stride,
+                                        const uint8_t *d_lut, uint64_t *d_out, size_t out_stride,
+                                        size_t count);
+
 /* Key switch + modulus switch only: d_out receives count * (n+1) uint32
  * values round(a * 2N / 2^64) of the key-switched ciphertexts. */
 lvs_status lvs_keyswitch_batch_device(lvs_ctx *ctx, const uint64_t *d_in, size_t in_stride,

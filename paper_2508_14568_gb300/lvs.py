@@ -33,7 +33,7 @@ EXPORTS = [
     "lvs_edit_distance_preprocessed_batch", "lvs_result_info", "lvs_result_export", "lvs_result_free",
     "lvs_decrypt", "lvs_decrypt_all", "lvs_pbs_batch_device", "lvs_keyswitch_batch_device",
     "lvs_poly_mul_device", "lvs_ctx_set_timing", "lvs_ctx_kernel_stats", "lvs_ctx_pbs_count",
-    "lvs_ctx_launch_count", "lvs_ct_string_upload",
+    "lvs_ctx_launch_count", "lvs_ct_string_upload", "lvs_pbs_batch_device_noalloc",
 ]
 
 
@@ -121,6 +121,7 @@ def _declare(L):
         "lvs_ctx_pbs_count": ([vp, u64p], i32),
         "lvs_ctx_launch_count": ([vp, u64p], i32),
         "lvs_ct_string_upload": ([vp, vp], i32),
+        "lvs_pbs_batch_device_noalloc": ([vp, vp, sz, vp, vp, sz, sz], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -403,6 +404,13 @@ def lvs_decrypt_all(ck, r):
 
 def lvs_pbs_batch_device(ctx, d_in, in_stride, d_lut, d_out, out_stride, count):
     _check(lib().lvs_pbs_batch_device(ctx, _ptr(d_in), in_stride, _ptr(d_lut), _ptr(d_out), out_stride, count))
+
+
+def lvs_pbs_batch_device_noalloc(ctx, d_in, in_stride, d_lut, d_out, out_stride, count):
+    """Same as lvs_pbs_batch_device, without allocating: scratch in the
+    library's static device array (see include/lvs.h for the limit)."""
+    _check(lib().lvs_pbs_batch_device_noalloc(ctx, _ptr(d_in), in_stride, _ptr(d_lut), _ptr(d_out), out_stride,
+                                              count))
 
 
 def lvs_keyswitch_batch_device(ctx, d_in, in_stride, d_out, count):
