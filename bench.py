@@ -39,7 +39,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lvs", choices=["lvs", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--rate", type=float, default=200.0, help="config 5: arrivals per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="config 5: arrival window in seconds")
+    ap.add_argument("--slots", type=int, default=16, help="config 5: server slots (admitted queries)")
+    ap.add_argument("--serial-pairs", type=int, default=8,
+                    help="pairs run one at a time for the one-pair-at-a-time comparison (0: skip)")
     ap.add_argument("--pairs", type=int, default=None, help="override the number of pairs (small profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -340,6 +345,25 @@ def run_lvs(args):
     if trec:
         traffic = trec["dram_bytes_per_pbs"] * units_per_launch
 
+    # the plain one-pair-at-a-time GPU form on the same inputs (a sample of pairs)
+    serial = None
+    if rank == 0 and cfg in (2, 4) and args.serial_pairs > 0:
+        lat = []
+        cells_s = 0
+        for k in range(min(args.serial_pairs, len(pairs))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r1 = L.lvs_edit_distance_batch(ctx, [A_dev[k]], [B_dev[k]])
+            L.lvs_ctx_synchronize(ctx)
+            lat.append(time.perf_counter() - t0)
+            cells_s += len(pairs[k][0]) * len(pairs[k][1])
+            r1 = None
+        lat.sort()
+        serial = {"cells_per_s": cells_s / sum(lat), "pairs": len(lat),
+                  "latency_ms_p50": 1e3 * lat[len(lat) // 2], "latency_ms_max": 1e3 * lat[-1],
+                  "note": "each pair alone through lvs_edit_distance_batch (same inputs, same kernels)"}
+    batched_latency_ms = t_max * 1e3 / args.steps   # every pair of a batch completes at the end of its step
+
     # end to end: host strings in, decrypted distances out
     e2e = None
     if not args.no_e2e:
@@ -416,6 +440,9 @@ def run_lvs(args):
                          "peak_note": "%d SMs x %d int32 mul/clk x max SM clock (derived)" % (
                              SM_COUNT_NOMINAL, MUL32_PER_SM_CLK)},
             "kernels": {"blind_rotate": br, "keyswitch": ks},
+            "latency_ms": {"p50": batched_latency_ms, "p99": batched_latency_ms,
+                           "note": "batched: all pairs of a step complete together"},
+            "one_pair_at_a_time": serial,
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -426,10 +453,70 @@ def run_lvs(args):
     return 0
 
 
+def run_serving(args):
+    """Config 5: Poisson arrivals of encrypted 27-symbol queries (length
+    U[4,64]) against plaintext or encrypted references (U[4,64], 50/50) into the
+    continuous-batching server; latency = completion - arrival."""
+    import torch
+    from oracle import plain as P
+    from paper_2508_14568_gb300 import lvs as L
+    from paper_2508_14568_gb300 import workloads as W
+    arrivals = W.config5(rate=args.rate, duration=args.duration)
+    params = L.lvs_params_default()
+    ck, sk = L.lvs_keygen(params, 0)
+    ctx = L.lvs_ctx_create(sk, 0)
+    # encrypt everything before the clock starts (client side)
+    enc = []
+    for k, (t, q, ref, plain) in enumerate(arrivals):
+        qa = L.lvs_encrypt_string(ck, q, L.LVS_ALPHA_27, 5, 2 * k)
+        rb = None if plain else L.lvs_encrypt_string(ck, ref, L.LVS_ALPHA_27, 5, 2 * k + 1)
+        enc.append((qa, rb))
+    server = L.lvs_server_create(ctx, 64 << 30, args.slots)
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    tickets, submit_t, done_t, results = [], [], {}, {}
+    k = 0
+    while len(done_t) < len(arrivals):
+        now = time.perf_counter() - t0
+        while k < len(arrivals) and arrivals[k][0] <= now:
+            qa, rb = enc[k]
+            tk = L.lvs_server_submit(server, qa, ref_enc=rb) if rb is not None else \
+                L.lvs_server_submit(server, qa, ref_plain=arrivals[k][2])
+            tickets.append(tk)
+            submit_t.append(arrivals[k][0])
+            k += 1
+        for i, tk in enumerate(tickets):
+            if i not in done_t:
+                r = L.lvs_server_poll(server, tk)
+                if r is not None:
+                    done_t[i] = time.perf_counter() - t0
+                    results[i] = r
+        time.sleep(0.001)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = L.lvs_server_stats_get(server)
+    lat = sorted(done_t[i] - submit_t[i] for i in done_t)
+    ok = all(L.lvs_decrypt(ck, results[i], 0) == P.wf_distance(arrivals[i][1], arrivals[i][2]) for i in results)
+    cells = sum(len(q) * len(ref) for _, q, ref, _ in arrivals)
+    line = {"metric": "serving p50/p99 query latency", "config": {
+                "workload": "config 5: Poisson %.1f queries/s for %.0f s, 27 symbols, lengths U[4,64], "
+                            "plaintext/encrypted reference 50/50, budget 64 GB, %d slots" % (args.rate, args.duration, args.slots),
+                "queries": len(arrivals)},
+            "latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "max": 1e3 * lat[-1]},
+            "cells_per_s": cells / wall, "pbs_per_s": st["pbs"] / wall, "wall_s": wall,
+            "server": st, "all_distances_correct": ok, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == 5:
+        return run_serving(args)
     return run_lvs(args)
 
 

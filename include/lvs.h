@@ -214,6 +214,51 @@ lvs_status lvs_decrypt(const lvs_client_key *ck, const lvs_result *r, size_t pai
 /* Decrypts every item of a result; dist has room for `items` values. */
 lvs_status lvs_decrypt_all(const lvs_client_key *ck, const lvs_result *r, uint32_t *dist);
 
+/* ---------------------------------------------------------------- serving */
+
+/* One query: an encrypted string against an encrypted reference (ref_enc,
+ * same alphabet family) or against a plaintext reference held by the server
+ * (ref_enc = NULL, ref_plain[0..ref_plain_len) in the query's alphabet).  The
+ * plaintext case first builds the Section 5 table for the symbols occurring in
+ * the reference (2 |S| m PBS, 1 for DNA), then runs one cell PBS per cell. */
+typedef struct lvs_query {
+    const lvs_ct_string *query;
+    const lvs_ct_string *ref_enc;
+    const uint8_t *ref_plain;
+    size_t ref_plain_len;
+} lvs_query;
+
+typedef struct lvs_server_stats {
+    uint64_t submitted, admitted, completed;
+    uint64_t pending, active;   /* queue depth and admitted queries now          */
+    uint64_t steps;             /* launch steps run                              */
+    uint64_t pbs;               /* PBS run                                       */
+    uint64_t max_step_pbs;      /* widest launch step                            */
+    uint64_t mem_in_use;        /* device bytes held by admitted queries         */
+    double busy_ms;             /* wall time spent inside launch steps           */
+} lvs_server_stats;
+
+/* Continuous batching (Section 6.2 parallelism across cells and across
+ * queries): a worker thread owned by the server runs launch steps on the
+ * context's stream; each step bootstraps the union of the next anti-diagonal
+ * work of every admitted query; queries are admitted in arrival order while
+ * a slot is free (at most max_active admitted queries; 0 = no slot limit) and
+ * their device footprint (ciphertext state, frontier, tables, result) fits
+ * mem_budget_bytes (one query is always admitted when none runs).  The
+ * context must not be used by other threads while the server exists. */
+lvs_status lvs_server_create(lvs_ctx *ctx, size_t mem_budget_bytes, size_t max_active, lvs_server **out);
+/* Copies the query (the caller may free its strings afterwards) and returns a
+ * ticket.  LVS_ERR_ARG if a symbol is outside the alphabet or the query alone
+ * exceeds the budget. */
+lvs_status lvs_server_submit(lvs_server *s, const lvs_query *q, uint64_t *ticket);
+/* LVS_OK and the result (one item: m, n, encrypted h[m][1..n]; the caller owns
+ * it) once the query is done; LVS_ERR_STATE while it is pending or running;
+ * LVS_ERR_ARG for an unknown or already collected ticket. */
+lvs_status lvs_server_poll(lvs_server *s, uint64_t ticket, lvs_result **out);
+lvs_status lvs_server_stats_get(lvs_server *s, lvs_server_stats *out);
+/* Stops the worker after its current step; unfinished queries are dropped. */
+void lvs_server_free(lvs_server *s);
+
 /* ---------------------------------------------------------------- low level */
 
 /* PBS on device buffers (Section 2.2; key switch -> modulus switch -> blind

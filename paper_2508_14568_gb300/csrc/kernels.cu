@@ -51,9 +51,9 @@ __device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][16], const uin
     using Lay = Layout<LOGN>;
     constexpr int N = Lay::N, T = Lay::T;
     const uint32_t p = c_pc.p[g], pinv = c_pc.pinv_neg[g];
-    ntt_forward<LOGN, 4>(d, buf, tau, twf, p, 1 + g);
+    ntt_forward4<LOGN>(d, reinterpret_cast<uint4 *>(buf), tau, twf, p, 1 + g);
 
-    uint32_t o[2][16];
+    // pointwise: out_c = sum_r D_r * K[r][c] (Montgomery), written over D_0, D_1
     const uint4 *kp = reinterpret_cast<const uint4 *>(key + (size_t)tau * 8);
     uint4 ka = __ldg(kp), kb = __ldg(kp + 1);
 #pragma unroll
@@ -71,16 +71,16 @@ __device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][16], const uin
         // slot = row * 2 + column
         const uint64_t t0 = (uint64_t)d0 * ka.x + (uint64_t)d1 * ka.z + (uint64_t)d2 * kb.x + (uint64_t)d3 * kb.z;
         const uint64_t t1 = (uint64_t)d0 * ka.y + (uint64_t)d1 * ka.w + (uint64_t)d2 * kb.y + (uint64_t)d3 * kb.w;
-        o[0][q] = redc(t0, p, pinv);
-        o[1][q] = redc(t1, p, pinv);
+        d[0][q] = redc(t0, p, pinv);
+        d[1][q] = redc(t1, p, pinv);
         if (q + 1 < 16) { ka = na; kb = nb; }
     }
-    ntt_inverse<LOGN, 2>(o, buf, tau, twi, p, 1 + g);
+    ntt_inverse2<LOGN>(d, reinterpret_cast<uint2 *>(buf), tau, twi, p, 1 + g);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         const uint32_t e = tau | ((uint32_t)q << Lay::B0);
-        crt[(g * 2 + 0) * N + e] = csub(o[0][q], p);
-        crt[(g * 2 + 1) * N + e] = csub(o[1][q], p);
+        crt[(g * 2 + 0) * N + e] = csub(d[0][q], p);
+        crt[(g * 2 + 1) * N + e] = csub(d[1][q], p);
     }
 }
 
@@ -115,8 +115,8 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
     const uint2 *twf = tw + (size_t)(g * 2 + 0) * N;
     const uint2 *twi = tw + (size_t)(g * 2 + 1) * N;
     const uint32_t B = 1u << base_log, hB = B >> 1;
-    const uint32_t shift = 64 - 2 * base_log;
-    const uint64_t round = 1ull << (shift - 1);
+    const uint32_t hshift = 64 - 2 * base_log - 32;   // shift - 32
+    const uint32_t hround = 1u << (hshift - 1);       // 2^(shift - 33)
     const size_t key_row = (size_t)3 * 16 * T * 8;   // u32 per BSK index i
 
     for (uint32_t job = blockIdx.x; job < njobs; job += gridDim.x) {
@@ -139,26 +139,29 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
         for (uint32_t i = 0; i < n; ++i) {
             const uint32_t a = __ldg(msj + i);
             if (a == 0) continue;   // X^0 ACC - ACC = 0: the external product is exactly 0
-            // decomposition of X^a ACC - ACC into 2 balanced digits per coefficient
+            // decomposition of X^a ACC - ACC into 2 balanced digits per coefficient.
+            // Only the rounded top 2*base_log bits of x are used: with shift =
+            // 64 - 2*base_log >= 32, (x + 2^(shift-1)) >> shift equals
+            // (hi32(x) + 2^(shift-33)) >> (shift-32) (the low word cannot carry).
             uint32_t d[4][16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const uint32_t e = tau | ((uint32_t)q << Lay::B0);
                 const uint32_t idx = (e - a) & (2 * N - 1);
+                const bool wrap = idx >= (uint32_t)N;
+                const uint32_t src = idx & (N - 1);
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const uint64_t cur = acc[j * N + e];
-                    uint64_t rv = acc[j * N + (idx & (N - 1))];
-                    if (idx >= (uint32_t)N) rv = 0 - rv;
-                    const uint64_t x = rv - cur;
-                    const uint64_t v = (x + round) >> shift;
-                    const uint32_t u2 = (uint32_t)v & (B - 1), u1 = (uint32_t)(v >> base_log) & (B - 1);
+                    const uint64_t rv = acc[j * N + src];
+                    const uint64_t x = wrap ? (0 - rv - cur) : (rv - cur);
+                    const uint32_t v = ((uint32_t)(x >> 32) + hround) >> hshift;
+                    const uint32_t u2 = v & (B - 1);
                     const uint32_t c2 = u2 >= hB;
-                    const int32_t d2 = (int32_t)u2 - (int32_t)(c2 * B);
-                    const uint32_t r1 = u1 + c2;
-                    const int32_t d1 = (int32_t)r1 - (int32_t)((r1 >= hB) * B);
-                    d[2 * j + 0][q] = d1 < 0 ? (uint32_t)(d1 + (int32_t)p) : (uint32_t)d1;
-                    d[2 * j + 1][q] = d2 < 0 ? (uint32_t)(d2 + (int32_t)p) : (uint32_t)d2;
+                    const uint32_t r1 = ((v >> base_log) & (B - 1)) + c2;
+                    // residues of the balanced digits: d < 0 -> d + p (values < 2p are fine for the NTT)
+                    d[2 * j + 1][q] = c2 ? u2 + (p - B) : u2;
+                    d[2 * j + 0][q] = r1 >= hB ? r1 + (p - B) : r1;
                 }
             }
             ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 16 * T * 8, buf, crt, tau, g,
@@ -266,20 +269,19 @@ k_keyswitch(const Job *__restrict__ jobs, uint32_t njobs,
     }
     if (c > n) return;
     const uint32_t twoN_mask = (1u << log2_2N) - 1;
-#pragma unroll 1
+#pragma unroll
     for (int jj = 0; jj < KS_TJ; ++jj) {
         const uint32_t j = j0 + jj;
-        if (j >= njobs) break;
-        uint64_t val = 0 - acc[jj];
-        if (c == n) {
-            uint64_t bb = (uint64_t)(sj[jj].cst & 31) << kDeltaLog;
-            for (int s = 0; s < 3; ++s)
-                if (sj[jj].src[s])
-                    bb += (uint64_t)(int64_t)sj[jj].coef[s] * sj[jj].src[s][big];
-            val += bb;
+        if (j < njobs) {
+            uint64_t val = 0 - acc[jj];
+            if (c == n) {
+                uint64_t bb = (uint64_t)(sj[jj].cst & 31) << kDeltaLog;
+                for (int s = 0; s < 3; ++s)
+                    if (sj[jj].src[s]) bb += (uint64_t)(int64_t)sj[jj].coef[s] * sj[jj].src[s][big];
+                val += bb;
+            }
+            ms[(size_t)j * (n + 1) + c] = (uint32_t)((val + (1ull << (63 - log2_2N))) >> (64 - log2_2N)) & twoN_mask;
         }
-        ms[(size_t)j * (n + 1) + c] =
-            (uint32_t)((val + (1ull << (63 - log2_2N))) >> (64 - log2_2N)) & twoN_mask;
     }
 }
 
@@ -312,7 +314,7 @@ k_bsk_to_ntt(const uint64_t *__restrict__ coef, uint32_t count, uint32_t *__rest
             v[k][q] = residue_of_signed((int64_t)src[e], p);
         }
     }
-    ntt_forward<LOGN, 4>(v, bufs + g * 4 * N, tau, tw + (size_t)(g * 2) * N, p, 1 + g);
+    ntt_forward4<LOGN>(v, reinterpret_cast<uint4 *>(bufs + g * 4 * N), tau, tw + (size_t)(g * 2) * N, p, 1 + g);
     const uint32_t m = g == 0 ? m0 : (g == 1 ? m1 : m2), msh = g == 0 ? ms0 : (g == 1 ? ms1 : ms2);
     uint32_t *dst = out + (size_t)i * 3 * 16 * T * 8 + (size_t)g * 16 * T * 8 + (size_t)tau * 8 + 4 * h;
 #pragma unroll

@@ -183,6 +183,42 @@ void make_prime_consts(dev::PrimeConsts &pc);
 void make_mont(uint32_t N, uint32_t mont[3][2]);
 void make_luts(std::vector<uint8_t> &table);   // [256][16]
 
+// ----------------------------------------------------------------- planner (sched.cu)
+struct Arena {
+    uint64_t *d = nullptr;
+    size_t stride = 0;
+    size_t rows = 0;
+    uint64_t *row(size_t r) const { return d + r * stride; }
+};
+
+// Per pair plan: the rows of its strings, frontier and rings.
+struct PairRows {
+    size_t m = 0, n = 0;
+    uint32_t C = 2;          // equality lookups per cell (2 ASCII / 27, 1 DNA)
+    size_t x = 0, y = 0;     // first arena row of a / b (row = first + char * C + symbol)
+    const uint64_t *xd = nullptr, *yd = nullptr;   // device-resident strings (else arena rows)
+    size_t xs = 0, ys = 0;                         // their row strides
+    size_t v = 0, h = 0;     // v[i] at v + i - 1, h[j] at h + j - 1
+    size_t eq1 = 0, eq9 = 0; // ring rows: + (d & 1) * m + i - 1
+    const uint64_t *table = nullptr;   // preprocessed path: rows T[row][i]
+    size_t table_stride = 0;
+    const int32_t *row_of = nullptr;
+    const uint8_t *plain = nullptr;
+};
+
+lvs_status arena_alloc(lvs_ctx *ctx, size_t rows, Arena &A);
+void arena_free(lvs_ctx *ctx, Arena &A);
+lvs_status upload_string(lvs_ctx *ctx, const lvs_ct_string *s, const Arena &A, size_t first);
+Job make_job(const uint64_t *s0, int c0, const uint64_t *s1, int c1, const uint64_t *s2, int c2, int cst,
+             uint8_t lut, uint8_t kind, uint64_t *d0, uint64_t *d1);
+lvs_status make_result(lvs_ctx *ctx, size_t rows, lvs_result **out);
+lvs_status finish_result(lvs_ctx *ctx, lvs_result *r);
+// jobs of wavefront step s of one pair (cells of anti-diagonal s - depth, etc.)
+void plan_pair_step(const PairRows &P, const Arena &A, long s, std::vector<Job> &jobs);
+// number of steps of one pair (0 if it has no cell)
+long pair_steps(const PairRows &P);
+lvs_status check_ctx_string(const lvs_ctx *ctx, const lvs_ct_string *s);
+
 // scratch and timing (ctx.cu)
 lvs_status ensure_scratch(lvs_ctx *ctx, size_t njobs_total, size_t njobs_step);
 lvs_status run_steps(lvs_ctx *ctx, const std::vector<Job> &jobs, const std::vector<size_t> &step_off,

@@ -19,9 +19,12 @@
 //   L1: e = hi << (logN-4) | q << (logN-8) | lo,   tau = hi << (logN-8) | lo
 //                                          stages 4..7
 //   L2: e = tau << 4 | q                   stages 8..logN-1
-// with shared-memory exchanges between passes, addressed through the swizzle
-// e ^ ((e >> 4) & 31), which is bank-conflict free for all three layouts.
-// L1 <-> L2 exchanges stay inside a warp; L0 <-> L1 needs the group barrier.
+// with shared-memory exchanges between passes.  The four forward polynomials
+// of a position travel as one 16-byte word (two inverse polynomials as one
+// 8-byte word), stored at the swizzled index e ^ ((e >> 4) & 7) (16 B) or
+// e ^ ((e >> 4) & 15) (8 B), which is bank-conflict free for all three
+// layouts.  L1 <-> L2 exchanges stay inside a warp; L0 <-> L1 needs the group
+// barrier.
 #pragma once
 #include <cstdint>
 
@@ -63,8 +66,6 @@ __device__ __forceinline__ uint32_t redc(uint64_t T, uint32_t p, uint32_t pinv_n
     return (uint32_t)((T + (uint64_t)m * p) >> 32);
 }
 
-__device__ __forceinline__ uint32_t swz(uint32_t e) { return e ^ ((e >> 4) & 31u); }
-
 __device__ __forceinline__ void group_bar(int id, int nthreads)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -87,8 +88,8 @@ struct Layout {
 
 // One register pass of forward (Cooley-Tukey) stages s0 .. s0+cnt-1 on NP
 // polynomials that share positions (and hence twiddles).
-template <int LOGN, int B, int S0, int CNT, int NP>
-__device__ __forceinline__ void fwd_pass(uint32_t (&v)[NP][16], uint32_t base, const uint2 *__restrict__ tw,
+template <int LOGN, int B, int S0, int CNT, int NP, int NPA>
+__device__ __forceinline__ void fwd_pass(uint32_t (&v)[NPA][16], uint32_t base, const uint2 *__restrict__ tw,
                                          uint32_t p)
 {
     const uint32_t p2 = 2 * p;
@@ -116,8 +117,8 @@ __device__ __forceinline__ void fwd_pass(uint32_t (&v)[NP][16], uint32_t base, c
 }
 
 // One register pass of inverse (Gentleman-Sande) stages s0+cnt-1 .. s0.
-template <int LOGN, int B, int S0, int CNT, int NP>
-__device__ __forceinline__ void inv_pass(uint32_t (&v)[NP][16], uint32_t base, const uint2 *__restrict__ tw,
+template <int LOGN, int B, int S0, int CNT, int NP, int NPA>
+__device__ __forceinline__ void inv_pass(uint32_t (&v)[NPA][16], uint32_t base, const uint2 *__restrict__ tw,
                                          uint32_t p)
 {
     const uint32_t p2 = 2 * p;
@@ -143,70 +144,91 @@ __device__ __forceinline__ void inv_pass(uint32_t (&v)[NP][16], uint32_t base, c
     }
 }
 
-// store / load the NP polynomials of a thread in layout (B, base) to/from
-// buf[k * N + swz(e)]
-template <int LOGN, int B, int NP>
-__device__ __forceinline__ void st_layout(uint32_t *buf, const uint32_t (&v)[NP][16], uint32_t base)
+// 16-byte words: index e ^ ((e >> 4) & 7).  8-byte words: the same per-warp
+// byte region as the 16-byte view (a warp of the L1/L2 layouts owns the 512
+// positions e >> 9 == warp, i.e. 16-byte words [512 w, 512 w + 512)), so that
+// a warp never writes 8-byte words into another warp's 16-byte region:
+// index ((e >> 9) << 10) | ((e ^ ((e >> 4) & 15)) & 511).
+__device__ __forceinline__ uint32_t swz16(uint32_t e) { return e ^ ((e >> 4) & 7u); }
+__device__ __forceinline__ uint32_t swz8(uint32_t e) { return ((e >> 9) << 10) | ((e ^ ((e >> 4) & 15u)) & 511u); }
+
+// store / load the polynomials of a thread in layout (B, base): 4 polynomials
+// per 16-byte word (forward) or 2 per 8-byte word (inverse)
+template <int LOGN, int B, int NPA>
+__device__ __forceinline__ void st4(uint4 *buf, const uint32_t (&v)[NPA][16], uint32_t base)
+{
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        buf[swz16(base | ((uint32_t)q << B))] = make_uint4(v[0][q], v[1][q], v[2][q], v[3][q]);
+}
+
+template <int LOGN, int B, int NPA>
+__device__ __forceinline__ void ld4(const uint4 *buf, uint32_t (&v)[NPA][16], uint32_t base)
 {
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-        const uint32_t a = swz(base | ((uint32_t)q << B));
-#pragma unroll
-        for (int k = 0; k < NP; ++k) buf[k * (1 << LOGN) + a] = v[k][q];
+        const uint4 w = buf[swz16(base | ((uint32_t)q << B))];
+        v[0][q] = w.x; v[1][q] = w.y; v[2][q] = w.z; v[3][q] = w.w;
     }
 }
 
-template <int LOGN, int B, int NP>
-__device__ __forceinline__ void ld_layout(const uint32_t *buf, uint32_t (&v)[NP][16], uint32_t base)
+template <int LOGN, int B, int NPA>
+__device__ __forceinline__ void st2(uint2 *buf, const uint32_t (&v)[NPA][16], uint32_t base)
+{
+#pragma unroll
+    for (int q = 0; q < 16; ++q) buf[swz8(base | ((uint32_t)q << B))] = make_uint2(v[0][q], v[1][q]);
+}
+
+template <int LOGN, int B, int NPA>
+__device__ __forceinline__ void ld2(const uint2 *buf, uint32_t (&v)[NPA][16], uint32_t base)
 {
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-        const uint32_t a = swz(base | ((uint32_t)q << B));
-#pragma unroll
-        for (int k = 0; k < NP; ++k) v[k][q] = buf[k * (1 << LOGN) + a];
+        const uint2 w = buf[swz8(base | ((uint32_t)q << B))];
+        v[0][q] = w.x; v[1][q] = w.y;
     }
 }
 
-// Full forward transform of NP polynomials held in L0 layout; returns them in
-// L2 layout (bit-reversed evaluation order), values in [0, 4p).
-// buf: NP * N words of this group's shared memory.  bar_id: group barrier.
-template <int LOGN, int NP>
-__device__ __forceinline__ void ntt_forward(uint32_t (&v)[NP][16], uint32_t *buf, uint32_t tau,
-                                            const uint2 *__restrict__ tw, uint32_t p, int bar_id)
+// Full forward transform of the 4 polynomials held in L0 layout; returns them
+// in L2 layout (bit-reversed evaluation order), values in [0, 4p).
+// buf: N 16-byte words of this group's shared memory.  bar_id: group barrier.
+template <int LOGN>
+__device__ __forceinline__ void ntt_forward4(uint32_t (&v)[4][16], uint4 *buf, uint32_t tau,
+                                             const uint2 *__restrict__ tw, uint32_t p, int bar_id)
 {
     using Lay = Layout<LOGN>;
-    fwd_pass<LOGN, Lay::B0, 0, 4, NP>(v, Lay::base0(tau), tw, p);
+    fwd_pass<LOGN, Lay::B0, 0, 4, 4, 4>(v, Lay::base0(tau), tw, p);
     __syncwarp();
-    st_layout<LOGN, Lay::B0, NP>(buf, v, Lay::base0(tau));
+    st4<LOGN, Lay::B0, 4>(buf, v, Lay::base0(tau));
     if (Lay::T > 32) group_bar(bar_id, Lay::T); else __syncwarp();
-    ld_layout<LOGN, Lay::B1, NP>(buf, v, Lay::base1(tau));
-    fwd_pass<LOGN, Lay::B1, 4, 4, NP>(v, Lay::base1(tau), tw, p);
+    ld4<LOGN, Lay::B1, 4>(buf, v, Lay::base1(tau));
+    fwd_pass<LOGN, Lay::B1, 4, 4, 4, 4>(v, Lay::base1(tau), tw, p);
     __syncwarp();
-    st_layout<LOGN, Lay::B1, NP>(buf, v, Lay::base1(tau));
+    st4<LOGN, Lay::B1, 4>(buf, v, Lay::base1(tau));
     __syncwarp();
-    ld_layout<LOGN, 0, NP>(buf, v, Lay::base2(tau));
-    fwd_pass<LOGN, 0, 8, Lay::S2, NP>(v, Lay::base2(tau), tw, p);
+    ld4<LOGN, 0, 4>(buf, v, Lay::base2(tau));
+    fwd_pass<LOGN, 0, 8, Lay::S2, 4, 4>(v, Lay::base2(tau), tw, p);
 }
 
-// Inverse transform of NP polynomials held in L2 layout (values in [0, 2p));
-// returns them in L0 layout (natural order), values in [0, 2p), NOT scaled by
-// N^{-1}.
-template <int LOGN, int NP>
-__device__ __forceinline__ void ntt_inverse(uint32_t (&v)[NP][16], uint32_t *buf, uint32_t tau,
-                                            const uint2 *__restrict__ tw, uint32_t p, int bar_id)
+// Inverse transform of the first 2 polynomials of v, held in L2 layout (values
+// in [0, 2p)); returns them in L0 layout (natural order), values in [0, 2p),
+// NOT scaled by N^{-1}.
+template <int LOGN>
+__device__ __forceinline__ void ntt_inverse2(uint32_t (&v)[4][16], uint2 *buf, uint32_t tau,
+                                             const uint2 *__restrict__ tw, uint32_t p, int bar_id)
 {
     using Lay = Layout<LOGN>;
-    inv_pass<LOGN, 0, 8, Lay::S2, NP>(v, Lay::base2(tau), tw, p);
+    inv_pass<LOGN, 0, 8, Lay::S2, 2, 4>(v, Lay::base2(tau), tw, p);
     __syncwarp();
-    st_layout<LOGN, 0, NP>(buf, v, Lay::base2(tau));
+    st2<LOGN, 0, 4>(buf, v, Lay::base2(tau));
     __syncwarp();
-    ld_layout<LOGN, Lay::B1, NP>(buf, v, Lay::base1(tau));
-    inv_pass<LOGN, Lay::B1, 4, 4, NP>(v, Lay::base1(tau), tw, p);
+    ld2<LOGN, Lay::B1, 4>(buf, v, Lay::base1(tau));
+    inv_pass<LOGN, Lay::B1, 4, 4, 2, 4>(v, Lay::base1(tau), tw, p);
     __syncwarp();
-    st_layout<LOGN, Lay::B1, NP>(buf, v, Lay::base1(tau));
+    st2<LOGN, Lay::B1, 4>(buf, v, Lay::base1(tau));
     if (Lay::T > 32) group_bar(bar_id, Lay::T); else __syncwarp();
-    ld_layout<LOGN, Lay::B0, NP>(buf, v, Lay::base0(tau));
-    inv_pass<LOGN, Lay::B0, 0, 4, NP>(v, Lay::base0(tau), tw, p);
+    ld2<LOGN, Lay::B0, 4>(buf, v, Lay::base0(tau));
+    inv_pass<LOGN, Lay::B0, 0, 4, 2, 4>(v, Lay::base0(tau), tw, p);
 }
 
 // Garner reconstruction of the signed integer with residues r0, r1, r2

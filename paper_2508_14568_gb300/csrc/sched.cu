@@ -22,15 +22,6 @@
 
 namespace lvs {
 
-namespace {
-
-struct Arena {
-    uint64_t *d = nullptr;
-    size_t stride = 0;
-    size_t rows = 0;
-    uint64_t *row(size_t r) const { return d + r * stride; }
-};
-
 lvs_status arena_alloc(lvs_ctx *ctx, size_t rows, Arena &A)
 {
     A.stride = (size_t)ctx->P.big() + 2;
@@ -98,24 +89,9 @@ lvs_status finish_result(lvs_ctx *ctx, lvs_result *r)
     return LVS_OK;
 }
 
-// Per pair plan: the rows of its strings, frontier and rings in the arena.
-struct PairRows {
-    size_t m = 0, n = 0;
-    uint32_t C = 2;          // equality lookups per cell (2 ASCII / 27, 1 DNA)
-    size_t x = 0, y = 0;     // first arena row of a / b (row = first + char * C + symbol)
-    const uint64_t *xd = nullptr, *yd = nullptr;   // device-resident strings (else arena rows)
-    size_t xs = 0, ys = 0;                         // their row strides
-    size_t v = 0, h = 0;     // v[i] at v + i - 1, h[j] at h + j - 1
-    size_t eq1 = 0, eq9 = 0; // ring rows: + (d & 1) * m + i - 1
-    const uint64_t *table = nullptr;   // preprocessed path: rows T[sym][i]
-    size_t table_stride = 0;
-    const int32_t *row_of = nullptr;
-    const uint8_t *plain = nullptr;
-};
-
 // cells (i, j) with i + j - 2 = d, 1 <= i <= m, 1 <= j <= n
 template <class F>
-void for_diag(const PairRows &P, long d, F f)
+static void for_diag(const PairRows &P, long d, F f)
 {
     if (d < 0 || P.m == 0 || P.n == 0) return;
     const long lo = std::max<long>(1, d + 2 - (long)P.n), hi = std::min<long>((long)P.m, d + 1);
@@ -167,15 +143,18 @@ void plan_pair_step(const PairRows &P, const Arena &A, long s, std::vector<Job> 
     }
 }
 
-// Runs the wavefront over all pairs; rows already placed.  Returns jobs count.
-lvs_status run_wavefront(lvs_ctx *ctx, const std::vector<PairRows> &pairs, const Arena &A, bool use_graph)
+long pair_steps(const PairRows &P)
+{
+    if (P.m == 0 || P.n == 0) return 0;
+    const long depth = P.table ? 0 : (long)P.C;
+    return (long)(P.m + P.n - 2) + depth + 1;
+}
+
+// Runs the wavefront over all pairs; rows already placed.
+static lvs_status run_wavefront(lvs_ctx *ctx, const std::vector<PairRows> &pairs, const Arena &A, bool use_graph)
 {
     long steps = 0;
-    for (const auto &P : pairs) {
-        if (P.m == 0 || P.n == 0) continue;
-        const long depth = P.table ? 0 : (long)P.C;
-        steps = std::max(steps, (long)(P.m + P.n - 2) + depth + 1);
-    }
+    for (const auto &P : pairs) steps = std::max(steps, pair_steps(P));
     std::vector<Job> jobs;
     std::vector<size_t> off{0};
     for (long s = 0; s < steps; ++s) {
@@ -192,7 +171,6 @@ lvs_status check_ctx_string(const lvs_ctx *ctx, const lvs_ct_string *s)
     return LVS_OK;
 }
 
-}  // namespace
 }  // namespace lvs
 
 using namespace lvs;

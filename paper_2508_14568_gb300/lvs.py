@@ -34,6 +34,7 @@ EXPORTS = [
     "lvs_decrypt", "lvs_decrypt_all", "lvs_pbs_batch_device", "lvs_keyswitch_batch_device",
     "lvs_poly_mul_device", "lvs_ctx_set_timing", "lvs_ctx_kernel_stats", "lvs_ctx_pbs_count",
     "lvs_ctx_launch_count", "lvs_ct_string_upload", "lvs_pbs_batch_device_noalloc",
+    "lvs_server_create", "lvs_server_submit", "lvs_server_poll", "lvs_server_stats_get", "lvs_server_free",
 ]
 
 
@@ -54,6 +55,19 @@ class lvs_params(ctypes.Structure):
 
 class lvs_opts(ctypes.Structure):
     _fields_ = [("band", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class lvs_query(ctypes.Structure):
+    _fields_ = [("query", ctypes.c_void_p), ("ref_enc", ctypes.c_void_p), ("ref_plain", ctypes.c_char_p),
+                ("ref_plain_len", ctypes.c_size_t)]
+
+
+class lvs_server_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "admitted", "completed", "pending", "active", "steps",
+                                               "pbs", "max_step_pbs", "mem_in_use")] + [("busy_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class lvs_kernel_stats(ctypes.Structure):
@@ -122,6 +136,11 @@ def _declare(L):
         "lvs_ctx_launch_count": ([vp, u64p], i32),
         "lvs_ct_string_upload": ([vp, vp], i32),
         "lvs_pbs_batch_device_noalloc": ([vp, vp, sz, vp, vp, sz, sz], i32),
+        "lvs_server_create": ([vp, sz, sz, vpp], i32),
+        "lvs_server_submit": ([vp, ctypes.POINTER(lvs_query), ctypes.POINTER(u64)], i32),
+        "lvs_server_poll": ([vp, u64, vpp], i32),
+        "lvs_server_stats_get": ([vp, ctypes.POINTER(lvs_server_stats)], i32),
+        "lvs_server_free": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -186,6 +205,10 @@ class Result(_Handle):
 
 class EqTable(_Handle):
     _free = "lvs_eq_table_free"
+
+
+class Server(_Handle):
+    _free = "lvs_server_free"
 
 
 # ------------------------------------------------------------------ params
@@ -398,6 +421,39 @@ def lvs_decrypt_all(ck, r):
     out = np.zeros(max(1, n), np.uint32)
     _check(lib().lvs_decrypt_all(ck, r, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
     return [int(x) for x in out[:n]]
+
+
+# ------------------------------------------------------------------ serving
+
+def lvs_server_create(ctx, mem_budget_bytes, max_active=0):
+    out = ctypes.c_void_p()
+    _check(lib().lvs_server_create(ctx, mem_budget_bytes, max_active, ctypes.byref(out)))
+    return Server(out.value, owner=ctx)
+
+
+def lvs_server_submit(server, query, ref_enc=None, ref_plain=None):
+    """query, ref_enc: CtString; ref_plain: str/bytes (used when ref_enc is None)."""
+    rp = _bytes(ref_plain) if ref_plain is not None else None
+    q = lvs_query(query.ptr, ref_enc.ptr if ref_enc is not None else None, rp, len(rp) if rp is not None else 0)
+    t = ctypes.c_uint64()
+    _check(lib().lvs_server_submit(server, ctypes.byref(q), ctypes.byref(t)))
+    return t.value
+
+
+def lvs_server_poll(server, ticket):
+    """Result when done, None while pending/running."""
+    out = ctypes.c_void_p()
+    st = lib().lvs_server_poll(server, ticket, ctypes.byref(out))
+    if st == LVS_ERR_STATE:
+        return None
+    _check(st)
+    return Result(out.value)
+
+
+def lvs_server_stats_get(server):
+    s = lvs_server_stats()
+    _check(lib().lvs_server_stats_get(server, ctypes.byref(s)))
+    return s.as_dict()
 
 
 # ------------------------------------------------------------------ low level (device pointers)
