@@ -154,12 +154,48 @@ def lut_from_key(keyfn):
     return f[:16]
 
 
+def key_eq2_swapped(dv_in, dh_in, eq):
+    """Eq. eq_keyeq2 with the roles of dv_in and dh_in exchanged:
+    (1 - dh_in) + 3 (1 + dv_in) + 9 eq."""
+    return key_eq2(dh_in, dv_in, eq)
+
+
+def lut_out_from_key(keyfn, outfn):
+    """The 16-entry LUT of an output outfn(dv_in, dh_in, eq) (in Z_32) as a
+    function of the key keyfn.  Keys 16 and 17 fall in the negacyclic half:
+    the table is only valid if out(16 + x) = -out(x) mod 32 there, which is
+    asserted.  Unused keys are 0."""
+    f = [None] * 18
+    for eq in (0, 1):
+        for dh in (-1, 0, 1):
+            for dv in (-1, 0, 1):
+                x = keyfn(dv, dh, eq)
+                o = outfn(dv, dh, eq) % PLAIN_MOD
+                assert 0 <= x < 18
+                assert f[x] in (None, o), "key is not injective on the output"
+                f[x] = o
+    for x in (16, 17):
+        if f[x] is not None:
+            assert f[x - 16] is not None and (f[x] + f[x - 16]) % PLAIN_MOD == 0, "not negacyclic"
+    f = [0 if v is None else v for v in f]
+    return f[:16]
+
+
+def lvs_refresh_v(dv_in, dh_in, eq):
+    """dv_out of Section 3.1.1 as one function of the cell inputs: M - dh_in."""
+    return lvs_M(dv_in, dh_in, eq) - dh_in
+
+
 LUT_MIN_PRINTED = None   # filled below: Table LUTmin (key of Eq. eq_keyeq)
 LUT_MIN = None           # key of Eq. eq_keyeq2, used by Algorithms alg_levenshtein / algo_complete
 LUT_EQ = [1] + [0] * 15  # Eq. eq_eqlut
 LUT_EQ9 = [9] + [0] * 15  # Eq. eq_eqlut9
 LUT_MIN_PRINTED = lut_from_key(key_eq)
 LUT_MIN = lut_from_key(key_eq2)
+# Refreshed cell (Section 3.1.3, refresh of dv and dh by a bootstrap): dv_out
+# straight from the key, and dh_out = M - dv_in from the swapped key through the
+# same table (M is symmetric in dv_in and dh_in).
+LUT_V = lut_out_from_key(key_eq2, lvs_refresh_v)
 
 
 def lookup(lut16, x):

@@ -311,8 +311,15 @@ def encrypt_string(keys, s, alphabet, noise_seed, string_id):
     return out
 
 
-def lvs_encrypted(keys, xa, yb, alphabet, parallel=False):
-    """Algorithm algo_complete on ciphertexts.
+def lvs_encrypted(keys, xa, yb, alphabet, parallel=False, band=None, refresh=()):
+    """Algorithm algo_complete on ciphertexts (with ``band``: only the cells
+    with |i - j| <= band, the condition of Algorithm alg_levenshtein; the
+    others keep the OneMatrix value 1).
+
+    ``refresh``: anti-diagonals d = i + j whose dv, dh are refreshed by a
+    bootstrap (Section 3.1.3): such a cell takes two lookups through LUT_V,
+    v[i][j] = PBS(key; LUT_V) and h[i][j] = PBS(key'; LUT_V) with the swapped
+    key' = (1 - h[i-1][j]) + 3 (1 + v[i][j-1]) + eq9, instead of M.
 
     xa, yb: lists (per character) of lists (per symbol) of ciphertexts.
 
@@ -329,8 +336,9 @@ def lvs_encrypted(keys, xa, yb, alphabet, parallel=False):
     both orders give identical ciphertexts.
 
     Returns a dict with the PBS outputs per cell ('eq1', 'eq9', 'M'), the
-    final row h[m][1..n] ('h_row'), the final column v[1..m][n] ('v_col') and
-    the number of PBS.
+    final row h[m][1..n] ('h_row'), the final column v[1..m][n] ('v_col'),
+    for square pairs the diagonal path [v[1][0], h[1][1], ..., v[m][m-1],
+    h[m][m]] ('diag', the readout of Section 3.2) and the number of PBS.
     """
     m, n = len(xa), len(yb)
     one = trivial(keys, 1)
@@ -346,17 +354,25 @@ def lvs_encrypted(keys, xa, yb, alphabet, parallel=False):
     def z_second(i, j, e1):
         return scalar(2, xa[i - 1][1] - yb[j - 1][1]) + (one - e1)
 
+    def inside(i, j):
+        return band is None or abs(i - j) <= band
+
     def key_of(i, j):
-        return (one - v[(i, j - 1)]) + scalar(3, one + h[(i - 1, j)]) + res["eq9"][(i, j)]
+        return (one - v.get((i, j - 1), one)) + scalar(3, one + h.get((i - 1, j), one)) + res["eq9"][(i, j)]
+
+    def key_swapped(i, j):
+        return (one - h.get((i - 1, j), one)) + scalar(3, one + v.get((i, j - 1), one)) + res["eq9"][(i, j)]
 
     def update(i, j, M):
         res["M"][(i, j)] = M
-        v[(i, j)] = M - h[(i - 1, j)]
-        h[(i, j)] = M - v[(i, j - 1)]
+        v[(i, j)] = M - h.get((i - 1, j), one)
+        h[(i, j)] = M - v.get((i, j - 1), one)
 
     if not parallel:
         for j in range(1, n + 1):
             for i in range(1, m + 1):
+                if not inside(i, j):
+                    continue
                 if dna:
                     res["eq9"][(i, j)] = pbs(keys, z_first(i, j), P.LUT_EQ9)
                     npbs += 1
@@ -365,10 +381,16 @@ def lvs_encrypted(keys, xa, yb, alphabet, parallel=False):
                     res["eq1"][(i, j)] = e1
                     res["eq9"][(i, j)] = pbs(keys, z_second(i, j, e1), P.LUT_EQ9)
                     npbs += 2
+                if i + j in refresh:
+                    nv = pbs(keys, key_of(i, j), P.LUT_V)
+                    nh = pbs(keys, key_swapped(i, j), P.LUT_V)
+                    v[(i, j)], h[(i, j)] = nv, nh
+                    npbs += 2
+                    continue
                 update(i, j, pbs(keys, key_of(i, j), P.LUT_MIN))
                 npbs += 1
     else:
-        cells = [(i, j) for j in range(1, n + 1) for i in range(1, m + 1)]
+        cells = [(i, j) for j in range(1, n + 1) for i in range(1, m + 1) if inside(i, j)]
         if dna:
             e9 = _pbs_list(keys, [z_first(i, j) for (i, j) in cells], P.LUT_EQ9)
             npbs += len(cells)
@@ -381,13 +403,22 @@ def lvs_encrypted(keys, xa, yb, alphabet, parallel=False):
         for c, e in zip(cells, e9):
             res["eq9"][c] = e
         for d in range(2, m + n + 1):
-            diag = [(i, d - i) for i in range(max(1, d - n), min(m, d - 1) + 1)]
+            diag = [(i, d - i) for i in range(max(1, d - n), min(m, d - 1) + 1) if inside(i, d - i)]
+            if d in refresh:
+                nvs = _pbs_list(keys, [key_of(i, j) for (i, j) in diag], P.LUT_V)
+                nhs = _pbs_list(keys, [key_swapped(i, j) for (i, j) in diag], P.LUT_V)
+                npbs += 2 * len(diag)
+                for c, nv, nh in zip(diag, nvs, nhs):
+                    v[c], h[c] = nv, nh
+                continue
             Ms = _pbs_list(keys, [key_of(i, j) for (i, j) in diag], P.LUT_MIN)
             npbs += len(diag)
             for (i, j), M in zip(diag, Ms):
                 update(i, j, M)
-    res["h_row"] = [h[(m, j)] for j in range(1, n + 1)]
-    res["v_col"] = [v[(i, n)] for i in range(1, m + 1)]
+    res["h_row"] = [h.get((m, j), one) for j in range(1, n + 1)]
+    res["v_col"] = [v.get((i, n), one) for i in range(1, m + 1)]
+    if m == n:
+        res["diag"] = [c for i in range(1, m + 1) for c in (v.get((i, i - 1), one), h.get((i, i), one))]
     res["pbs"] = npbs
     return res
 
@@ -399,6 +430,11 @@ def _pbs_list(keys, cts, lut):
     luts = np.tile(np.asarray(lut, dtype=np.uint32), (len(cts), 1))
     out = pbs_many(keys, arr, luts)
     return [out[i] for i in range(len(cts))]
+
+
+def decrypt_path(keys, cts, base=0):
+    """base + the decrypted differences along a path of the matrix."""
+    return base + sum(P.signed(decrypt(keys, c)) for c in cts)
 
 
 def decrypt_distance(keys, h_row, m):

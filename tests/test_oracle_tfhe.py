@@ -278,3 +278,24 @@ def test_lvs_encrypted_paper_order_equals_diagonal_order(keys):
         for c in r1[name]:
             assert np.array_equal(r1[name][c], r2[name][c])
     assert T.decrypt_distance(keys, r1["h_row"], 3) == P.wf_distance(a, b)
+
+
+def test_lvs_encrypted_band_exact_skip_and_approx(keys):
+    """Algorithm alg_levenshtein's band on ciphertexts: the diagonal readout
+    equals Wagner-Fischer with the exact-skip band floor(m/2) (Section 3.2),
+    and the plaintext banded oracle with a narrow band; fewer PBS."""
+    for a, b, band in [("abcd", "bcda", 2), ("kitten", "sittin", 3), ("aaaaa", "bbbaa", 1)]:
+        xa = T.encrypt_string(keys, a, P.ALPHA_ASCII7, 31, 0)
+        yb = T.encrypt_string(keys, b, P.ALPHA_ASCII7, 31, 1)
+        res = T.lvs_encrypted(keys, xa, yb, P.ALPHA_ASCII7, parallel=True, band=band)
+        m = len(a)
+        E9 = [[0] * (m + 1) for _ in range(m + 1)]
+        for i in range(1, m + 1):
+            for j in range(1, m + 1):
+                E9[i][j] = 9 if a[i - 1] == b[j - 1] else 0
+        h, v = P.lvs_on_eq9(E9, m, m, band=band)
+        want = P.readout_diagonal(h, v, m)
+        assert T.decrypt_path(keys, res["diag"]) == want
+        if band >= m // 2:
+            assert want == P.wf_distance(a, b)
+        assert res["pbs"] == 3 * P.band_cells(m, band)
