@@ -160,11 +160,41 @@ lvs_status lvs_encrypt_lwe(const lvs_client_key *ck, uint32_t value, uint64_t no
 /* Edit-distance options.  band < 0: exact full matrix (the configurations of
  * this library compute every cell). */
 typedef struct lvs_opts {
-    int32_t band;          /* reserved: must be -1 (full matrix)                 */
+    int32_t band;          /* < 0: full matrix.  >= 0: only the cells with      *
+                            * |i - j| <= band (Algorithm alg_levenshtein), for   *
+                            * pairs with m = n; band = floor(m/2) is exact       *
+                            * ("Exact Skip", Section 3.2), smaller bands give    *
+                            * the approximate distance of Section 3.2            */
     int32_t use_graph;     /* 1: capture the wavefront launches in a CUDA graph  */
-    int32_t reserved[6];
+    int32_t refresh_budget;/* noise budget of a key, in units of the variance   *
+                            * of a fresh PBS output (Section 3.1.3; the paper's  *
+                            * example parameter set allows 25).  0: from the     *
+                            * parameter set for a failure probability of 2^-64   *
+                            * per PBS (lvs_noise_budget); > 0: this budget;      *
+                            * < 0: never refresh.  Anti-diagonals chosen by      *
+                            * lvs_noise_plan are refreshed: their cells take two *
+                            * PBS (dv and dh as fresh bootstrap outputs) instead *
+                            * of one.  LVS_ERR_NOISE_BUDGET if no plan fits.     */
+    int32_t reserved[5];
 } lvs_opts;
 void lvs_opts_default(lvs_opts *o);
+
+/* Noise budget (Section 3.1.3): the largest variance of a key, in units of
+ * the variance of a fresh PBS output, for which one bootstrap of it (with
+ * the key-switch and modulus-switch noise of the parameter set, binary keys
+ * of expected weight) decodes wrongly with probability at most 2^log2_pfail
+ * (log2_pfail < 0).  Host only. */
+lvs_status lvs_noise_budget(const lvs_params *p, double log2_pfail, double *budget);
+/* Refresh plan of one m x n difference matrix (band < 0: full; else cells
+ * with |i - j| <= band).  Each M and EQ9 is a unit noise, dv_out = M - dh_in,
+ * dh_out = M - dv_in; a cell costs the larger variance of its key and of its
+ * key with dv_in, dh_in exchanged.  An anti-diagonal d = i + j is refreshed
+ * when, without it, a cell of d + 1 would cost more than budget (budget <= 0:
+ * no refresh).  refresh (may be NULL): m + n + 1 bytes, refresh[d] = 1 for
+ * the refreshed anti-diagonals; max_key_var (may be NULL): the largest cost.
+ * LVS_ERR_NOISE_BUDGET if a cell exceeds the budget even so.  Host only. */
+lvs_status lvs_noise_plan(size_t m, size_t n, int32_t band, double budget, uint8_t *refresh,
+                          double *max_key_var);
 
 /* Encrypted equality of characters a[i] and b[j] (Algorithm alg_ascii: 2 PBS
  * for ASCII7 / 27 symbols; Section 4.1: 1 PBS for DNA4).  times9 != 0 gives
@@ -179,6 +209,9 @@ lvs_status lvs_eq(lvs_ctx *ctx, const lvs_ct_string *a, size_t i, const lvs_ct_s
  * s-1, EQ1 of s} (Section 6.2 "Parallelism": cells of one anti-diagonal are
  * independent).  The result holds, per pair, the encrypted last row
  * h[m][1..n] and the plaintext m; the distance is m + sum_j dec(h[m][j]).
+ * With a band (opts->band >= 0) the result holds instead the diagonal path
+ * [v[1][0], h[1][1], ..., v[m][m-1], h[m][m]] (2m ciphertexts) and the
+ * distance is its decrypted sum (Section 3.2 readout).
  * Both strings of a pair must share the alphabet; lengths may be 0. */
 lvs_status lvs_edit_distance_batch(lvs_ctx *ctx, const lvs_ct_string *const *a,
                                    const lvs_ct_string *const *b, size_t npairs,
@@ -272,6 +305,24 @@ lvs_status lvs_pbs_batch_device(lvs_ctx *ctx, const uint64_t *d_in, size_t in_st
                                 const uint8_t *d_lut, uint64_t *d_out, size_t out_stride,
                                 size_t count);
 
+/* FP64-FFT variant of the blind rotation (the paper's implementation relies
+ * on TFHE-rs, whose bootstrap multiplies polynomials with a double-precision
+ * FFT; Section 2.2 defines the PBS itself).  lvs_ctx_prepare_fft64 converts
+ * the server key's bootstrapping key into the FFT domain on the context's
+ * device (n * 8 * N/2 complex doubles: 109 MB at the default parameters, owned
+ * by the context and freed with it); sk must be the key the context was made
+ * from (LVS_ERR_ARG if its parameters differ).  A second call does nothing.
+ * Synchronous.  lvs_pbs_batch_device_fft64 then takes the arguments of
+ * lvs_pbs_batch_device and computes the same function with FFT products: the
+ * outputs are not bit-identical to the exact NTT path (the key and the
+ * products are rounded to 53-bit mantissas, an error far below the bootstrap
+ * noise), but decrypt to the same messages.  LVS_ERR_STATE if the context has
+ * no FFT key. */
+lvs_status lvs_ctx_prepare_fft64(lvs_ctx *ctx, const lvs_server_key *sk);
+lvs_status lvs_pbs_batch_device_fft64(lvs_ctx *ctx, const uint64_t *d_in, size_t in_stride,
+                                      const uint8_t *d_lut, uint64_t *d_out, size_t out_stride,
+                                      size_t count);
+
 /* Allocation-free variant of lvs_pbs_batch_device (the paper has no
  * counterpart; this is a service of the library).  For callers that cannot
  * allocate device memory while they run -- a server that reserves its whole
@@ -283,9 +334,9 @@ lvs_status lvs_pbs_batch_device(lvs_ctx *ctx, const uint64_t *d_in, size_t in_st
  * the modulus-switched masks passed from the key-switch kernel to the
  * blind-rotation kernel) lives in one static device array of
  * LVS_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
- * process exits.  Limit: count * (48 + 4 (n+1)) bytes + 256 must fit, i.e. at
- * most 1237 PBS per call for n = 834 (13617 for n = 64); larger counts fail
- * with LVS_ERR_ARG and do nothing.  The first call on a device looks up the
+ * process exits.  Limit: count * (64 + 4 (n+1)) bytes plus up to 255 bytes of
+ * alignment must fit, i.e. at most 1232 PBS per call for n = 834 (12944 for
+ * n = 64); larger counts fail with LVS_ERR_ARG and do nothing.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call before
  * any stream capture.  All calls share the one array and every call rewrites
  * the part it uses before reading it (nothing needs to start at zero): calls

@@ -204,6 +204,7 @@ lvs_status lvs_ctx_create(const lvs_server_key *sk, int device, void *stream, lv
     if (cudaMalloc((void **)&ctx->tw, tw.size() * 4) != cudaSuccess ||
         cudaMalloc((void **)&ctx->luts, luts.size()) != cudaSuccess ||
         cudaMalloc((void **)&ctx->ksk, sk->ksk.size() * 8) != cudaSuccess ||
+        cudaMalloc((void **)&ctx->ksk_colsum, ((size_t)n + 1) * 8) != cudaSuccess ||
         cudaMalloc((void **)&ctx->bsk_ntt, bsk_ntt * 4) != cudaSuccess) {
         cudaGetLastError();
         return fail(set_error(LVS_ERR_OOM, "device allocation of the server key failed"));
@@ -217,6 +218,7 @@ lvs_status lvs_ctx_create(const lvs_server_key *sk, int device, void *stream, lv
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->luts, luts.data(), luts.size(), cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->ksk, sk->ksk.data(), sk->ksk.size() * 8, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = launch_ksk_colsum(ctx, ctx->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(coef, sk->bsk.data(), sk->bsk.size() * 8, cudaMemcpyHostToDevice, ctx->stream);
     uint32_t mont[3][2];
@@ -239,8 +241,11 @@ void lvs_ctx_free(lvs_ctx *ctx)
     for (auto e : ctx->timing.pool) cudaEventDestroy(e);
     cudaFree(ctx->bsk_ntt);
     cudaFree(ctx->ksk);
+    cudaFree(ctx->ksk_colsum);
     cudaFree(ctx->tw);
     cudaFree(ctx->luts);
+    cudaFree(ctx->bsk_fft);
+    cudaFree(ctx->fft_tw);
     if (ctx->ms) cudaFree(ctx->ms);
     if (ctx->jobs) cudaFree(ctx->jobs);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);

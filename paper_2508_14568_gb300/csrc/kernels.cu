@@ -88,7 +88,7 @@ __device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][16], const uin
 template <int LOGN>
 struct BrSmem {
     static constexpr int N = 1 << LOGN;
-    static constexpr size_t acc_bytes = 2 * N * sizeof(uint64_t);
+    static constexpr size_t acc_bytes = 2 * 2 * N * sizeof(uint64_t);   // negacyclically extended
     static constexpr size_t buf_bytes = 3 * 4 * N * sizeof(uint32_t);
     static constexpr size_t crt_bytes = 3 * 2 * N * sizeof(uint32_t);
     static constexpr size_t total = acc_bytes + buf_bytes + crt_bytes;
@@ -114,7 +114,7 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
     const uint32_t p = c_pc.p[g];
     const uint2 *twf = tw + (size_t)(g * 2 + 0) * N;
     const uint2 *twi = tw + (size_t)(g * 2 + 1) * N;
-    const uint32_t B = 1u << base_log, hB = B >> 1;
+    const uint32_t B = 1u << base_log, hB = B >> 1, pmB = p - B;
     const uint32_t hshift = 64 - 2 * base_log - 32;   // shift - 32
     const uint32_t hround = 1u << (hshift - 1);       // 2^(shift - 33)
     const size_t key_row = (size_t)3 * 16 * T * 8;   // u32 per BSK index i
@@ -128,40 +128,38 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
             const uint4 lv = *reinterpret_cast<const uint4 *>(lp);
             memcpy(f, &lv, 16);
         }
-        // ACC = (0, X^{-b} v')
+        // ACC = (0, X^{-b} v'), kept negacyclically extended: acc[j][t + N] =
+        // -acc[j][t], so that (X^a ACC)[e] = acc[j][(e - a) mod 2N] is a plain read
         const uint32_t b = __ldg(msj + n);
-        for (int e = tid; e < N; e += NT) {
-            acc[e] = 0;
-            acc[N + e] = test_poly_at<LOGN>(f, (e + b) & (2 * N - 1));
+        for (int t = tid; t < 2 * N; t += NT) {
+            acc[t] = 0;
+            acc[2 * N + t] = test_poly_at<LOGN>(f, (t + b) & (2 * N - 1));
         }
         __syncthreads();
 
         for (uint32_t i = 0; i < n; ++i) {
             const uint32_t a = __ldg(msj + i);
             if (a == 0) continue;   // X^0 ACC - ACC = 0: the external product is exactly 0
-            // decomposition of X^a ACC - ACC into 2 balanced digits per coefficient.
-            // Only the rounded top 2*base_log bits of x are used: with shift =
-            // 64 - 2*base_log >= 32, (x + 2^(shift-1)) >> shift equals
-            // (hi32(x) + 2^(shift-33)) >> (shift-32) (the low word cannot carry).
+            // digits of X^a ACC - ACC.  Only the rounded top 2*base_log bits of
+            // x are used: with shift = 64 - 2*base_log >= 32,
+            // (x + 2^(shift-1)) >> shift = (hi32(x) + 2^(shift-33)) >> (shift-32).
             uint32_t d[4][16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const uint32_t e = tau | ((uint32_t)q << Lay::B0);
-                const uint32_t idx = (e - a) & (2 * N - 1);
-                const bool wrap = idx >= (uint32_t)N;
-                const uint32_t src = idx & (N - 1);
+                const uint32_t src = (e - a) & (2 * N - 1);
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    const uint64_t cur = acc[j * N + e];
-                    const uint64_t rv = acc[j * N + src];
-                    const uint64_t x = wrap ? (0 - rv - cur) : (rv - cur);
+                    const uint64_t *A = acc + j * 2 * N;
+                    const uint64_t x = A[src] - A[e];
                     const uint32_t v = ((uint32_t)(x >> 32) + hround) >> hshift;
                     const uint32_t u2 = v & (B - 1);
-                    const uint32_t c2 = u2 >= hB;
-                    const uint32_t r1 = ((v >> base_log) & (B - 1)) + c2;
-                    // residues of the balanced digits: d < 0 -> d + p (values < 2p are fine for the NTT)
-                    d[2 * j + 1][q] = c2 ? u2 + (p - B) : u2;
-                    d[2 * j + 0][q] = r1 >= hB ? r1 + (p - B) : r1;
+                    const uint32_t c2 = u2 >> (base_log - 1);   // u2 >= B/2
+                    const uint32_t r1 = (v >> base_log) + c2;    // <= B
+                    const uint32_t c1 = (r1 + hB) >> base_log;   // r1 >= B/2 (r1 = B gives 1)
+                    // residues of the balanced digits (d < 0 -> d + p; < 2p is fine)
+                    d[2 * j + 1][q] = u2 + c2 * pmB;
+                    d[2 * j + 0][q] = r1 + c1 * pmB;
                 }
             }
             ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 16 * T * 8, buf, crt, tau, g,
@@ -171,25 +169,29 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
                 const int j = c >> LOGN, e = c & (N - 1);
                 const uint64_t x = crt3(crt[(0 * 2 + j) * N + e], crt[(1 * 2 + j) * N + e],
                                         crt[(2 * 2 + j) * N + e], c_pc);
-                acc[j * N + e] += x;
+                uint64_t *A = acc + j * 2 * N;
+                const uint64_t y = A[e] + x;
+                A[e] = y;
+                A[e + N] = 0 - y;
             }
             __syncthreads();
         }
 
-        // sample extract (coefficient 0) and epilogue
+        // sample extract (coefficient 0) and epilogue: a_0 = A[0], a_u = -A[N - u]
+        // = A[2N - u] (u > 0), b = B[0]
         uint64_t *o0 = J.dst[0];
         uint64_t *o1 = J.dst[1];
         for (int u = tid; u <= N; u += NT) {
-            uint64_t val;
-            if (u == N) val = acc[N];
-            else if (u == 0) val = acc[0];
-            else val = 0 - acc[N - u];
+            const uint64_t val = u == N ? acc[2 * N] : acc[(2 * N - u) & (2 * N - 1)];
             if (J.kind == JOB_CELL) {
                 const uint64_t vold = o0[u], hold = o1[u];
-                o0[u] = val - hold;   // v[i][j] = M - h[i-1][j]
-                o1[u] = val - vold;   // h[i][j] = M - v[i][j-1]
+                const uint64_t vn = val - hold, hn = val - vold;
+                o0[u] = vn;   // v[i][j] = M - h[i-1][j]
+                o1[u] = hn;   // h[i][j] = M - v[i][j-1]
+                if (J.tapsel) J.tap[u] = J.tapsel == 1 ? vn : hn;
             } else {
                 o0[u] = val;
+                if (J.tapsel) J.tap[u] = val;
             }
         }
         __syncthreads();
@@ -197,17 +199,22 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
 }
 
 // ---------------------------------------------------------------- key switch
+// out = (0, b) - sum_{u, lev} d_{u,lev} KSK[u][lev].  Digits are kept offset to
+// d' = d + B/2 in [0, B), so each product is unsigned: the low 32 bits of the
+// KSK word go through one 32x32->64 multiply-add into a 64-bit sum and the high
+// 32 bits through one 32-bit multiply-add (only needed mod 2^32); the offset
+// comes back as (B/2) * colsum[c], colsum[c] = sum_{u,lev} KSK[u][lev][c].
 constexpr int KS_TJ = 16;       // jobs per CTA
 constexpr int KS_THREADS = 128; // output columns per CTA
-constexpr int KS_UCH = 128;     // input coefficients per digit chunk
+constexpr int KS_UCH = 64;      // input coefficients per digit chunk
 constexpr int KS_MAXL = 8;
 
 __global__ void __launch_bounds__(KS_THREADS)
 k_keyswitch(const Job *__restrict__ jobs, uint32_t njobs,
-            const uint64_t *__restrict__ ksk, uint32_t n, uint32_t big, uint32_t ks_level, uint32_t ks_base_log,
-            uint32_t log2_2N, uint32_t *__restrict__ ms)
+            const uint64_t *__restrict__ ksk, const uint64_t *__restrict__ colsum, uint32_t n, uint32_t big,
+            uint32_t ks_level, uint32_t ks_base_log, uint32_t log2_2N, uint32_t *__restrict__ ms)
 {
-    __shared__ __align__(16) int8_t dig[KS_UCH][KS_MAXL][KS_TJ];
+    __shared__ __align__(16) uint32_t dig[KS_UCH][KS_MAXL][KS_TJ];
     __shared__ Job sj[KS_TJ];
     const int t = threadIdx.x;
     const uint32_t j0 = blockIdx.x * KS_TJ;
@@ -224,20 +231,22 @@ k_keyswitch(const Job *__restrict__ jobs, uint32_t njobs,
     const uint32_t beta = ks_level * ks_base_log;
     const uint64_t rnd = 1ull << (63 - beta);
     const uint32_t Bk = 1u << ks_base_log, hBk = Bk >> 1;
-    uint64_t acc[KS_TJ];
+    uint64_t lo[KS_TJ];
+    uint32_t hi[KS_TJ];
 #pragma unroll
-    for (int jj = 0; jj < KS_TJ; ++jj) acc[jj] = 0;
+    for (int jj = 0; jj < KS_TJ; ++jj) { lo[jj] = 0; hi[jj] = 0; }
 
+    // digit prologue: thread t covers coefficient u0 + (t % KS_UCH) of 8 jobs
+    const int tu = t % KS_UCH, tj = (t / KS_UCH) * (KS_TJ / 2);
     for (uint32_t u0 = 0; u0 < big; u0 += KS_UCH) {
-        const uint32_t u = u0 + t;
+        const uint32_t u = u0 + tu;
 #pragma unroll 1
-        for (int jj = 0; jj < KS_TJ; ++jj) {
+        for (int jj = tj; jj < tj + KS_TJ / 2; ++jj) {
             uint64_t a = 0;
             if (u < big) {
 #pragma unroll
                 for (int s = 0; s < 3; ++s)
-                    if (sj[jj].src[s])
-                        a += (uint64_t)(int64_t)sj[jj].coef[s] * __ldg(sj[jj].src[s] + u);
+                    if (sj[jj].src[s]) a += (uint64_t)(int64_t)sj[jj].coef[s] * __ldg(sj[jj].src[s] + u);
             }
             const uint64_t v = (a + rnd) >> (64 - beta);
             uint32_t carry = 0;
@@ -245,7 +254,7 @@ k_keyswitch(const Job *__restrict__ jobs, uint32_t njobs,
                 const uint32_t uu = (uint32_t)(v >> ((ks_level - lev) * ks_base_log)) & (Bk - 1);
                 const uint32_t r = uu + carry;
                 carry = r >= hBk;
-                dig[t][lev - 1][jj] = (int8_t)((int32_t)r - (int32_t)(carry * Bk));
+                dig[tu][lev - 1][jj] = r - carry * Bk + hBk;   // balanced digit + B/2
             }
         }
         __syncthreads();
@@ -255,12 +264,15 @@ k_keyswitch(const Job *__restrict__ jobs, uint32_t njobs,
                 const uint64_t *krow = ksk + ((size_t)(u0 + ul) * ks_level) * (n + 1) + c;
                 for (uint32_t lev = 0; lev < ks_level; ++lev) {
                     const uint64_t kv = __ldg(krow + (size_t)lev * (n + 1));
-                    const int4 dv = *reinterpret_cast<const int4 *>(&dig[ul][lev][0]);
-                    const int32_t w[4] = {dv.x, dv.y, dv.z, dv.w};
+                    const uint32_t klo = (uint32_t)kv, khi = (uint32_t)(kv >> 32);
+                    const uint4 *dp = reinterpret_cast<const uint4 *>(&dig[ul][lev][0]);
 #pragma unroll
-                    for (int jj = 0; jj < KS_TJ; ++jj) {
-                        const int32_t dd = (int32_t)(int8_t)(w[jj >> 2] >> ((jj & 3) * 8));
-                        acc[jj] += (uint64_t)(int64_t)dd * kv;
+                    for (int w = 0; w < KS_TJ / 4; ++w) {
+                        const uint4 dv = dp[w];
+                        lo[4 * w + 0] += (uint64_t)dv.x * klo; hi[4 * w + 0] += dv.x * khi;
+                        lo[4 * w + 1] += (uint64_t)dv.y * klo; hi[4 * w + 1] += dv.y * khi;
+                        lo[4 * w + 2] += (uint64_t)dv.z * klo; hi[4 * w + 2] += dv.z * khi;
+                        lo[4 * w + 3] += (uint64_t)dv.w * klo; hi[4 * w + 3] += dv.w * khi;
                     }
                 }
             }
@@ -269,11 +281,13 @@ k_keyswitch(const Job *__restrict__ jobs, uint32_t njobs,
     }
     if (c > n) return;
     const uint32_t twoN_mask = (1u << log2_2N) - 1;
+    const uint64_t offset = (uint64_t)hBk * colsum[c];
 #pragma unroll
     for (int jj = 0; jj < KS_TJ; ++jj) {
         const uint32_t j = j0 + jj;
         if (j < njobs) {
-            uint64_t val = 0 - acc[jj];
+            const uint64_t sum = lo[jj] + ((uint64_t)hi[jj] << 32) - offset;   // sum_{u,lev} d * KSK
+            uint64_t val = 0 - sum;
             if (c == n) {
                 uint64_t bb = (uint64_t)(sj[jj].cst & 31) << kDeltaLog;
                 for (int s = 0; s < 3; ++s)
@@ -283,6 +297,16 @@ k_keyswitch(const Job *__restrict__ jobs, uint32_t njobs,
             ms[(size_t)j * (n + 1) + c] = (uint32_t)((val + (1ull << (63 - log2_2N))) >> (64 - log2_2N)) & twoN_mask;
         }
     }
+}
+
+// colsum[c] = sum over all KSK rows of column c (mod 2^64), once per context
+__global__ void k_ksk_colsum(const uint64_t *__restrict__ ksk, uint32_t rows, uint32_t n, uint64_t *colsum)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > n) return;
+    uint64_t s = 0;
+    for (uint32_t r = 0; r < rows; ++r) s += ksk[(size_t)r * (n + 1) + c];
+    colsum[c] = s;
 }
 
 // ---------------------------------------------------------------- key conversion
@@ -430,8 +454,8 @@ cudaError_t launch_keyswitch(const lvs_ctx *ctx, const Job *jobs, size_t njobs, 
     const auto &p = ctx->P.p;
     dim3 grid((unsigned)((njobs + KS_TJ - 1) / KS_TJ), (p.n + 1 + KS_THREADS - 1) / KS_THREADS);
     const uint32_t log2_2N = ctx->P.log_n() + 1;
-    k_keyswitch<<<grid, KS_THREADS, 0, s>>>(jobs, (uint32_t)njobs, ctx->ksk, p.n, ctx->P.big(), p.ks_level,
-                                             p.ks_base_log, log2_2N, ms);
+    k_keyswitch<<<grid, KS_THREADS, 0, s>>>(jobs, (uint32_t)njobs, ctx->ksk, ctx->ksk_colsum, p.n, ctx->P.big(),
+                                             p.ks_level, p.ks_base_log, log2_2N, ms);
     return cudaGetLastError();
 }
 
@@ -448,6 +472,14 @@ cudaError_t launch_blind_rotate(const lvs_ctx *ctx, const Job *jobs, size_t njob
     else
         k_blind_rotate<9><<<grid, br_threads(p.N), BrSmem<9>::total, s>>>(
             jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ksk_colsum(const lvs_ctx *ctx, cudaStream_t s)
+{
+    const auto &p = ctx->P.p;
+    const uint32_t rows = ctx->P.big() * p.ks_level;
+    k_ksk_colsum<<<(p.n + 1 + 127) / 128, 128, 0, s>>>(ctx->ksk, rows, p.n, ctx->ksk_colsum);
     return cudaGetLastError();
 }
 

@@ -33,7 +33,7 @@ constexpr int kRows = 4;           // (k+1) * pbs_level with k = 1, level = 2
 constexpr int kMaxJobsPerLaunch = 1 << 20;
 
 // LUT ids in the context's LUT table
-enum : uint8_t { LUT_EQ = 0, LUT_EQ9 = 1, LUT_MIN = 2, LUT_USER0 = 8 };
+enum : uint8_t { LUT_EQ = 0, LUT_EQ9 = 1, LUT_MIN = 2, LUT_V = 3, LUT_USER0 = 8 };
 // job kinds (epilogue of the blind-rotation kernel)
 enum : uint8_t { JOB_STORE = 0, JOB_CELL = 1 };
 
@@ -43,17 +43,21 @@ enum : uint8_t { JOB_STORE = 0, JOB_CELL = 1 };
 //   STORE: *dst[0] = PBS
 //   CELL : M = PBS; *dst[0] (v) = M - *dst[1]_old (h),
 //                   *dst[1] (h) = M - *dst[0]_old (v)      (Section 3.1.1)
+//          and, for a cell on the readout path of a band, a copy of the new
+//          v (tapsel 1) or h (tapsel 2) to *tap.
 // All pointers are device rows of k*N+1 words.
 struct alignas(16) Job {
     const uint64_t *src[3];
     uint64_t *dst[2];
+    uint64_t *tap;
     int8_t coef[3];
     int8_t cst;
     uint8_t lut;
     uint8_t kind;
-    uint8_t pad[2];
+    uint8_t tapsel;
+    uint8_t pad[9];
 };
-static_assert(sizeof(Job) == 48, "Job layout");
+static_assert(sizeof(Job) == 64, "Job layout");
 
 // ----------------------------------------------------------------- host keys
 struct Params {
@@ -121,8 +125,13 @@ struct lvs_ctx {
     // device keys
     uint32_t *bsk_ntt = nullptr;   // [n][kPrimes][16][T][8] u32
     uint64_t *ksk = nullptr;       // [kN][ks_l][n+1]
+    uint64_t *ksk_colsum = nullptr; // [n+1]: column sums of the KSK
     uint32_t *tw = nullptr;        // twiddles: uint2 {w, w_shoup} [prime][fwd, inv][N]
     uint8_t *luts = nullptr;       // [256][16]
+    // optional FP64-FFT key (lvs_ctx_prepare_fft64)
+    double *bsk_fft = nullptr;     // [n][8][N/2] complex
+    double *fft_tw = nullptr;      // twiddles: [N/4] complex exp(2 pi i t/(N/2)), then [N/2] complex exp(i pi j/N)
+    int fft_grid = 0;
     // scratch (grown on demand; owned by the context)
     uint32_t *ms = nullptr;        // [ms_cap][n+1] modulus-switched masks of one launch
     size_t ms_cap = 0;
@@ -141,7 +150,8 @@ struct lvs_result {
     int device = 0;
     uint64_t *d = nullptr;            // device rows [total][stride], owned
     size_t stride = 0;                // words per row (>= k*N+1)
-    struct Item { size_t m, n, first, count; };
+    // distance = base + sum of the decrypted rows [first, first + count)
+    struct Item { size_t m, n, first, count; long base; };
     std::vector<Item> items;
     bool is_eq = false;
     cudaEvent_t done = nullptr;       // recorded after the producing launches
@@ -167,6 +177,7 @@ cudaError_t prepare_kernels(uint32_t N);
 cudaError_t launch_bsk_to_ntt_count(uint32_t N, const uint64_t *coef, uint32_t count, uint32_t *out,
                                     const uint32_t *tw, const uint32_t mont[3][2], cudaStream_t s);
 cudaError_t launch_keyswitch(const lvs_ctx *ctx, const Job *jobs, size_t njobs, uint32_t *ms, cudaStream_t s);
+cudaError_t launch_ksk_colsum(const lvs_ctx *ctx, cudaStream_t s);
 cudaError_t launch_blind_rotate(const lvs_ctx *ctx, const Job *jobs, size_t njobs, const uint32_t *ms,
                                 const uint8_t *luts, int lut_per_job, cudaStream_t s);
 cudaError_t launch_poly_mul(const lvs_ctx *ctx, const int32_t *dig, const uint32_t *keyntt, uint64_t *out,
@@ -204,6 +215,9 @@ struct PairRows {
     size_t table_stride = 0;
     const int32_t *row_of = nullptr;
     const uint8_t *plain = nullptr;
+    long band = -1;          // >= 0: only cells with |i - j| <= band (square pairs)
+    size_t tap = 0;          // band: 2m rows [v[1][0], h[1][1], ..., v[m][m-1], h[m][m]]
+    std::vector<uint8_t> refresh;   // empty, or [m + n + 1]: 1 if anti-diagonal i + j is refreshed
 };
 
 lvs_status arena_alloc(lvs_ctx *ctx, size_t rows, Arena &A);
@@ -218,6 +232,12 @@ void plan_pair_step(const PairRows &P, const Arena &A, long s, std::vector<Job> 
 // number of steps of one pair (0 if it has no cell)
 long pair_steps(const PairRows &P);
 lvs_status check_ctx_string(const lvs_ctx *ctx, const lvs_ct_string *s);
+
+// noise budget and refresh plan (noise.cu)
+double noise_budget(const lvs_params &p, double log2_pfail);
+lvs_status noise_plan(size_t m, size_t n, long band, double budget, std::vector<uint8_t> *refresh, double *worst);
+// refresh_budget: 0 = from the parameters (failure probability 2^-64), > 0 = explicit, < 0 = none
+lvs_status plan_refresh(const lvs_ctx *ctx, int32_t refresh_budget, PairRows &P);
 
 // scratch and timing (ctx.cu)
 lvs_status ensure_scratch(lvs_ctx *ctx, size_t njobs_total, size_t njobs_step);

@@ -153,38 +153,40 @@ __device__ __forceinline__ uint32_t swz16(uint32_t e) { return e ^ ((e >> 4) & 7
 __device__ __forceinline__ uint32_t swz8(uint32_t e) { return ((e >> 9) << 10) | ((e ^ ((e >> 4) & 15u)) & 511u); }
 
 // store / load the polynomials of a thread in layout (B, base): 4 polynomials
-// per 16-byte word (forward) or 2 per 8-byte word (inverse)
-template <int LOGN, int B, int NPA>
-__device__ __forceinline__ void st4(uint4 *buf, const uint32_t (&v)[NPA][16], uint32_t base)
+// per 16-byte word (forward) or 2 per 8-byte word (inverse).  Both swizzles are
+// linear over GF(2) and base and q << B occupy disjoint bits, so
+// swz(base | q << B) = swz(base) ^ swz(q << B): the callers pass sb = swz(base)
+// once and the per-q part is a compile-time constant.
+template <int B, int NPA>
+__device__ __forceinline__ void st4(uint4 *buf, const uint32_t (&v)[NPA][16], uint32_t sb)
 {
 #pragma unroll
-    for (int q = 0; q < 16; ++q)
-        buf[swz16(base | ((uint32_t)q << B))] = make_uint4(v[0][q], v[1][q], v[2][q], v[3][q]);
+    for (int q = 0; q < 16; ++q) buf[sb ^ swz16((uint32_t)q << B)] = make_uint4(v[0][q], v[1][q], v[2][q], v[3][q]);
 }
 
-template <int LOGN, int B, int NPA>
-__device__ __forceinline__ void ld4(const uint4 *buf, uint32_t (&v)[NPA][16], uint32_t base)
+template <int B, int NPA>
+__device__ __forceinline__ void ld4(const uint4 *buf, uint32_t (&v)[NPA][16], uint32_t sb)
 {
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-        const uint4 w = buf[swz16(base | ((uint32_t)q << B))];
+        const uint4 w = buf[sb ^ swz16((uint32_t)q << B)];
         v[0][q] = w.x; v[1][q] = w.y; v[2][q] = w.z; v[3][q] = w.w;
     }
 }
 
-template <int LOGN, int B, int NPA>
-__device__ __forceinline__ void st2(uint2 *buf, const uint32_t (&v)[NPA][16], uint32_t base)
+template <int B, int NPA>
+__device__ __forceinline__ void st2(uint2 *buf, const uint32_t (&v)[NPA][16], uint32_t sb)
 {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) buf[swz8(base | ((uint32_t)q << B))] = make_uint2(v[0][q], v[1][q]);
+    for (int q = 0; q < 16; ++q) buf[sb ^ swz8((uint32_t)q << B)] = make_uint2(v[0][q], v[1][q]);
 }
 
-template <int LOGN, int B, int NPA>
-__device__ __forceinline__ void ld2(const uint2 *buf, uint32_t (&v)[NPA][16], uint32_t base)
+template <int B, int NPA>
+__device__ __forceinline__ void ld2(const uint2 *buf, uint32_t (&v)[NPA][16], uint32_t sb)
 {
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-        const uint2 w = buf[swz8(base | ((uint32_t)q << B))];
+        const uint2 w = buf[sb ^ swz8((uint32_t)q << B)];
         v[0][q] = w.x; v[1][q] = w.y;
     }
 }
@@ -199,14 +201,15 @@ __device__ __forceinline__ void ntt_forward4(uint32_t (&v)[4][16], uint4 *buf, u
     using Lay = Layout<LOGN>;
     fwd_pass<LOGN, Lay::B0, 0, 4, 4, 4>(v, Lay::base0(tau), tw, p);
     __syncwarp();
-    st4<LOGN, Lay::B0, 4>(buf, v, Lay::base0(tau));
+    st4<Lay::B0, 4>(buf, v, swz16(Lay::base0(tau)));
     if (Lay::T > 32) group_bar(bar_id, Lay::T); else __syncwarp();
-    ld4<LOGN, Lay::B1, 4>(buf, v, Lay::base1(tau));
+    const uint32_t sb1 = swz16(Lay::base1(tau));
+    ld4<Lay::B1, 4>(buf, v, sb1);
     fwd_pass<LOGN, Lay::B1, 4, 4, 4, 4>(v, Lay::base1(tau), tw, p);
     __syncwarp();
-    st4<LOGN, Lay::B1, 4>(buf, v, Lay::base1(tau));
+    st4<Lay::B1, 4>(buf, v, sb1);
     __syncwarp();
-    ld4<LOGN, 0, 4>(buf, v, Lay::base2(tau));
+    ld4<0, 4>(buf, v, swz16(Lay::base2(tau)));
     fwd_pass<LOGN, 0, 8, Lay::S2, 4, 4>(v, Lay::base2(tau), tw, p);
 }
 
@@ -220,14 +223,15 @@ __device__ __forceinline__ void ntt_inverse2(uint32_t (&v)[4][16], uint2 *buf, u
     using Lay = Layout<LOGN>;
     inv_pass<LOGN, 0, 8, Lay::S2, 2, 4>(v, Lay::base2(tau), tw, p);
     __syncwarp();
-    st2<LOGN, 0, 4>(buf, v, Lay::base2(tau));
+    st2<0, 4>(buf, v, swz8(Lay::base2(tau)));
     __syncwarp();
-    ld2<LOGN, Lay::B1, 4>(buf, v, Lay::base1(tau));
+    const uint32_t sb1 = swz8(Lay::base1(tau));
+    ld2<Lay::B1, 4>(buf, v, sb1);
     inv_pass<LOGN, Lay::B1, 4, 4, 2, 4>(v, Lay::base1(tau), tw, p);
     __syncwarp();
-    st2<LOGN, Lay::B1, 4>(buf, v, Lay::base1(tau));
+    st2<Lay::B1, 4>(buf, v, sb1);
     if (Lay::T > 32) group_bar(bar_id, Lay::T); else __syncwarp();
-    ld2<LOGN, Lay::B0, 4>(buf, v, Lay::base0(tau));
+    ld2<Lay::B0, 4>(buf, v, swz8(Lay::base0(tau)));
     inv_pass<LOGN, Lay::B0, 0, 4, 2, 4>(v, Lay::base0(tau), tw, p);
 }
 

@@ -94,8 +94,44 @@ template <class F>
 static void for_diag(const PairRows &P, long d, F f)
 {
     if (d < 0 || P.m == 0 || P.n == 0) return;
-    const long lo = std::max<long>(1, d + 2 - (long)P.n), hi = std::min<long>((long)P.m, d + 1);
+    long lo = std::max<long>(1, d + 2 - (long)P.n), hi = std::min<long>((long)P.m, d + 1);
+    if (P.band >= 0) {
+        // |i - j| <= band with j = d + 2 - i  <=>  (d + 2 - band) / 2 <= i <= (d + 2 + band) / 2
+        lo = std::max(lo, (d + 2 - P.band + 1) / 2);
+        hi = std::min(hi, (d + 2 + P.band) / 2);
+    }
     for (long i = lo; i <= hi; ++i) f((size_t)i, (size_t)(d + 2 - i));
+}
+
+// band mode: cells (i, i-1) and (i, i) lie on the diagonal readout path
+// (Section 3.2: the distance is the sum of v and h along the diagonal);
+// they also copy their new v (resp. h) to the pair's tap rows.
+static Job tapped(const PairRows &P, const Arena &A, size_t i, size_t j, Job J)
+{
+    if (P.band < 0) return J;
+    if (j + 1 == i) { J.tap = A.row(P.tap + 2 * (i - 1)); J.tapsel = 1; }
+    else if (j == i) { J.tap = A.row(P.tap + 2 * (i - 1) + 1); J.tapsel = 2; }
+    return J;
+}
+
+// the cell PBS of (i, j): key = (1 - v[i][j-1]) + 3 (1 + h[i-1][j]) + EQ9 through
+// LUT_min with the in-place update of v[i] and h[j]; on a refreshed
+// anti-diagonal (Section 3.1.3) two PBS through LUT_V instead: v from the
+// key, h from the key with v and h exchanged, both fresh bootstrap outputs.
+static void cell_jobs(const PairRows &P, const Arena &A, size_t i, size_t j, const uint64_t *e9, uint64_t *Vi,
+                      uint64_t *Hj, std::vector<Job> &jobs)
+{
+    if (!P.refresh.empty() && P.refresh[i + j]) {
+        const Job t = tapped(P, A, i, j, Job{});
+        Job jv = make_job(Vi, -1, Hj, 3, e9, 1, 4, LUT_V, JOB_STORE, Vi, nullptr);
+        Job jh = make_job(Vi, 3, Hj, -1, e9, 1, 4, LUT_V, JOB_STORE, Hj, nullptr);
+        if (t.tapsel == 1) { jv.tap = t.tap; jv.tapsel = 1; }
+        if (t.tapsel == 2) { jh.tap = t.tap; jh.tapsel = 1; }
+        jobs.push_back(jv);
+        jobs.push_back(jh);
+        return;
+    }
+    jobs.push_back(tapped(P, A, i, j, make_job(Vi, -1, Hj, 3, e9, 1, 4, LUT_MIN, JOB_CELL, Vi, Hj)));
 }
 
 void plan_pair_step(const PairRows &P, const Arena &A, long s, std::vector<Job> &jobs)
@@ -114,7 +150,7 @@ void plan_pair_step(const PairRows &P, const Arena &A, long s, std::vector<Job> 
         // preprocessed: EQ9[i][j] = T[b_j][i], one cell PBS per cell
         for_diag(P, s, [&](size_t i, size_t j) {
             const uint64_t *t = P.table + ((size_t)P.row_of[P.plain[j - 1]] * P.m + (i - 1)) * P.table_stride;
-            jobs.push_back(make_job(V(i), -1, H(j), 3, t, 1, 4, LUT_MIN, JOB_CELL, V(i), H(j)));
+            cell_jobs(P, A, i, j, t, V(i), H(j), jobs);
         });
         return;
     }
@@ -130,7 +166,7 @@ void plan_pair_step(const PairRows &P, const Arena &A, long s, std::vector<Job> 
         });
         // cells of diagonal s-2: key = (1 - v[i][j-1]) + 3 (1 + h[i-1][j]) + EQ9
         for_diag(P, s - 2, [&](size_t i, size_t j) {
-            jobs.push_back(make_job(V(i), -1, H(j), 3, E9(s - 2, i), 1, 4, LUT_MIN, JOB_CELL, V(i), H(j)));
+            cell_jobs(P, A, i, j, E9(s - 2, i), V(i), H(j), jobs);
         });
     } else {
         // DNA: EQ9 = PBS(x_i - y_j; LUT_EQ9), one lookup
@@ -138,7 +174,7 @@ void plan_pair_step(const PairRows &P, const Arena &A, long s, std::vector<Job> 
             jobs.push_back(make_job(X(i, 0), 1, Y(j, 0), -1, nullptr, 0, 0, LUT_EQ9, JOB_STORE, E9(s, i), nullptr));
         });
         for_diag(P, s - 1, [&](size_t i, size_t j) {
-            jobs.push_back(make_job(V(i), -1, H(j), 3, E9(s - 1, i), 1, 4, LUT_MIN, JOB_CELL, V(i), H(j)));
+            cell_jobs(P, A, i, j, E9(s - 1, i), V(i), H(j), jobs);
         });
     }
 }
@@ -184,9 +220,9 @@ lvs_status lvs_edit_distance_batch(lvs_ctx *ctx, const lvs_ct_string *const *a, 
     lvs_opts o;
     lvs_opts_default(&o);
     if (opts) o = *opts;
-    if (o.band >= 0) return set_error(LVS_ERR_ARG, "lvs_edit_distance_batch: banded mode is not available");
+    const bool banded = o.band >= 0;
     std::vector<PairRows> pairs(npairs);
-    size_t rows = 0, xrows = 0, vrows = 0, hrows = 0, rrows = 0;
+    size_t rows = 0, xrows = 0, vrows = 0, hrows = 0, rrows = 0, trows = 0;
     for (size_t p = 0; p < npairs; ++p) {
         lvs_status st = check_ctx_string(ctx, a[p]);
         if (st == LVS_OK) st = check_ctx_string(ctx, b[p]);
@@ -199,6 +235,15 @@ lvs_status lvs_edit_distance_batch(lvs_ctx *ctx, const lvs_ct_string *const *a, 
         P.m = a[p]->len;
         P.n = b[p]->len;
         P.C = a[p]->symbols;
+        if (banded) {
+            // Section 3.2 / Section 6: the band and its diagonal readout are stated for m = n
+            if (P.m != P.n)
+                return set_error(LVS_ERR_ARG, "lvs_edit_distance_batch: the band needs equal lengths (pair " +
+                                                  std::to_string(p) + ")");
+            P.band = o.band;
+            trows += 2 * P.m;
+        }
+        if ((st = plan_refresh(ctx, o.refresh_budget, P)) != LVS_OK) return st;
         if (a[p]->d && a[p]->ddevice == ctx->device) { P.xd = a[p]->d; P.xs = a[p]->dstride; }
         else xrows += P.m * P.C;
         if (b[p]->d && b[p]->ddevice == ctx->device) { P.yd = b[p]->d; P.ys = b[p]->dstride; }
@@ -207,16 +252,17 @@ lvs_status lvs_edit_distance_batch(lvs_ctx *ctx, const lvs_ct_string *const *a, 
         hrows += P.n;
         rrows += (P.C == 2 ? 4 : 2) * P.m;
     }
-    // rows: [strings][v][h][rings]
-    rows = xrows + vrows + hrows + rrows;
+    // rows: [strings][v][h][band taps][rings]
+    rows = xrows + vrows + hrows + trows + rrows;
     LVS_CUDA(cudaSetDevice(ctx->device));
     std::lock_guard<std::mutex> lock(ctx->mu);
     Arena A;
     lvs_status st = arena_alloc(ctx, rows, A);
     if (st != LVS_OK) return st;
-    size_t cx = 0, cv = xrows, ch = xrows + vrows, cr = xrows + vrows + hrows;
+    size_t cx = 0, cv = xrows, ch = xrows + vrows, ct = xrows + vrows + hrows, cr = ct + trows;
     for (size_t p = 0; p < npairs; ++p) {
         PairRows &P = pairs[p];
+        if (banded) { P.tap = ct; ct += 2 * P.m; }
         if (!P.xd) { P.x = cx; cx += P.m * P.C; }
         if (!P.yd) { P.y = cx; cx += P.n * P.C; }
         P.v = cv; cv += P.m;
@@ -229,24 +275,28 @@ lvs_status lvs_edit_distance_batch(lvs_ctx *ctx, const lvs_ct_string *const *a, 
             return st;
         }
     }
-    // OneMatrix boundary: v[i][0] = h[0][j] = 1 as noiseless ciphertexts (0, Delta)
-    cudaError_t e = launch_fill_trivial(A.d, A.stride, ctx->P.big(), xrows, vrows + hrows, 1ull << kDeltaLog,
+    // OneMatrix boundary: v[i][0] = h[0][j] = 1 as noiseless ciphertexts (0, Delta);
+    // band taps start at 1 too (out-of-band path values keep the OneMatrix value)
+    cudaError_t e = launch_fill_trivial(A.d, A.stride, ctx->P.big(), xrows, vrows + hrows + trows, 1ull << kDeltaLog,
                                         ctx->stream);
     if (e != cudaSuccess) { arena_free(ctx, A); return cuda_error(e, "fill"); }
     ctx->launches += vrows + hrows ? 1 : 0;
     st = run_wavefront(ctx, pairs, A, o.use_graph != 0);
     if (st != LVS_OK) { arena_free(ctx, A); return st; }
     lvs_result *r = nullptr;
-    st = make_result(ctx, hrows, &r);
+    // result rows: h[m][1..n] (distance m + sum), or the band's diagonal path (distance = sum)
+    const size_t out_rows = banded ? trows : hrows;
+    st = make_result(ctx, out_rows, &r);
     if (st != LVS_OK) { arena_free(ctx, A); return st; }
     size_t first = 0;
     for (size_t p = 0; p < npairs; ++p) {
-        r->items.push_back({pairs[p].m, pairs[p].n, first, pairs[p].n});
-        first += pairs[p].n;
+        const size_t cnt = banded ? 2 * pairs[p].m : pairs[p].n;
+        r->items.push_back({pairs[p].m, pairs[p].n, first, cnt, banded ? 0L : (long)pairs[p].m});
+        first += cnt;
     }
-    if (hrows) {
-        e = cudaMemcpy2DAsync(r->d, r->stride * 8, A.row(xrows + vrows), A.stride * 8, (ctx->P.big() + 1) * 8, hrows,
-                              cudaMemcpyDeviceToDevice, ctx->stream);
+    if (out_rows) {
+        e = cudaMemcpy2DAsync(r->d, r->stride * 8, A.row(banded ? xrows + vrows + hrows : xrows + vrows), A.stride * 8,
+                              (ctx->P.big() + 1) * 8, out_rows, cudaMemcpyDeviceToDevice, ctx->stream);
         if (e != cudaSuccess) { arena_free(ctx, A); lvs_result_free(r); return cuda_error(e, "result copy"); }
     }
     arena_free(ctx, A);
@@ -282,7 +332,7 @@ lvs_status lvs_eq(lvs_ctx *ctx, const lvs_ct_string *a, size_t i, const lvs_ct_s
     lvs_result *r = nullptr;
     if ((st = make_result(ctx, 1, &r)) != LVS_OK) { arena_free(ctx, A); return st; }
     r->is_eq = true;
-    r->items.push_back({1, 1, 0, 1});
+    r->items.push_back({1, 1, 0, 1, 0});
     const uint8_t last = times9 ? LUT_EQ9 : LUT_EQ;
     std::vector<Job> jobs;
     std::vector<size_t> off{0};
@@ -415,6 +465,8 @@ lvs_status lvs_edit_distance_preprocessed_batch(lvs_ctx *ctx, const lvs_eq_table
         P.table_stride = t[q]->stride;
         P.row_of = t[q]->row_of;
         P.plain = plain[q];
+        lvs_status st = plan_refresh(ctx, o.refresh_budget, P);
+        if (st != LVS_OK) return st;
         vrows += P.m;
         hrows += P.n;
     }
@@ -438,7 +490,7 @@ lvs_status lvs_edit_distance_preprocessed_batch(lvs_ctx *ctx, const lvs_eq_table
     lvs_result *r = nullptr;
     if ((st = make_result(ctx, hrows, &r)) != LVS_OK) { arena_free(ctx, A); return st; }
     size_t first = 0;
-    for (auto &P : pairs) { r->items.push_back({P.m, P.n, first, P.n}); first += P.n; }
+    for (auto &P : pairs) { r->items.push_back({P.m, P.n, first, P.n, (long)P.m}); first += P.n; }
     if (hrows) {
         e = cudaMemcpy2DAsync(r->d, r->stride * 8, A.row(vrows), A.stride * 8, (ctx->P.big() + 1) * 8, hrows,
                               cudaMemcpyDeviceToDevice, ctx->stream);
@@ -523,8 +575,9 @@ static lvs_status decrypt_rows(const lvs_client_key *ck, const lvs_result *r, co
         *out = decrypt_lwe(*ck, host);
         return LVS_OK;
     }
-    // D[m][n] = m + sum_{j=1..n} h[m][j], each h in {-1, 0, 1} (Z_32 residues)
-    long d = (long)it.m;
+    // D[m][n] = base + sum of the path differences, each in {-1, 0, 1} (Z_32
+    // residues): base m with the last row h[m][1..n], base 0 with the band path
+    long d = it.base;
     for (size_t j = 0; j < it.count; ++j) {
         const uint32_t v = decrypt_lwe(*ck, host + j * w);
         d += v >= 16 ? (long)v - 32 : (long)v;

@@ -84,6 +84,7 @@ lvs_status setup(lvs_ctx *ctx, Query &q)
     P.m = q.m;
     P.n = q.n;
     P.C = q.C;
+    if ((st = plan_refresh(ctx, 0, P)) != LVS_OK) return st;
     size_t r = 0;
     P.x = r; r += q.m * q.C;
     if ((st = upload_string(ctx, &q.q, q.A, P.x)) != LVS_OK) return st;
@@ -146,7 +147,7 @@ lvs_status finish(lvs_server *S, Query &q, lvs_result **out)
     lvs_result *r = nullptr;
     lvs_status st = make_result(ctx, q.n, &r);
     if (st != LVS_OK) return st;
-    r->items.push_back({q.m, q.n, 0, q.n});
+    r->items.push_back({q.m, q.n, 0, q.n, (long)q.m});
     if (q.n) {
         const cudaError_t e = cudaMemcpy2DAsync(r->d, r->stride * 8, q.A.row(q.P.h), q.A.stride * 8,
                                                 ((size_t)ctx->P.big() + 1) * 8, q.n, cudaMemcpyDeviceToDevice,

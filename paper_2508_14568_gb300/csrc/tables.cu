@@ -120,6 +120,10 @@ void make_mont(uint32_t N, uint32_t mont[3][2])
 //   LUT_MIN: M = 1 + min(-eq, dv, dh) as a function of the key
 //            (1 - dv) + 3 (1 + dh) + 9 eq of Eq. eq_keyeq2; keys 16 and 17 fall
 //            in the negacyclic half and need M = 0 there and at keys 0, 1.
+//   LUT_V  : dv_out = M - dh_in as a function of the same key (refreshed
+//            cells, Section 3.1.3); keys 16, 17 give -1 = -(value at 0, 1),
+//            so the negacyclic half holds.  With dv_in and dh_in exchanged in
+//            the key the same table gives dh_out (M is symmetric).
 void make_luts(std::vector<uint8_t> &t)
 {
     t.assign(256 * 16, 0);
@@ -130,7 +134,10 @@ void make_luts(std::vector<uint8_t> &t)
             for (int dv = -1; dv <= 1; ++dv) {
                 const int key = (1 - dv) + 3 * (1 + dh) + 9 * eq;
                 const int M = 1 + std::min(std::min(-eq, dv), dh);
-                if (key < 16) t[LUT_MIN * 16 + key] = (uint8_t)M;
+                if (key < 16) {
+                    t[LUT_MIN * 16 + key] = (uint8_t)M;
+                    t[LUT_V * 16 + key] = (uint8_t)((M - dh + 32) % 32);   // dv_out = M - dh_in
+                }
             }
 }
 

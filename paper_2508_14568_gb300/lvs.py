@@ -34,6 +34,7 @@ EXPORTS = [
     "lvs_decrypt", "lvs_decrypt_all", "lvs_pbs_batch_device", "lvs_keyswitch_batch_device",
     "lvs_poly_mul_device", "lvs_ctx_set_timing", "lvs_ctx_kernel_stats", "lvs_ctx_pbs_count",
     "lvs_ctx_launch_count", "lvs_ct_string_upload", "lvs_pbs_batch_device_noalloc",
+    "lvs_ctx_prepare_fft64", "lvs_pbs_batch_device_fft64", "lvs_noise_budget", "lvs_noise_plan",
     "lvs_server_create", "lvs_server_submit", "lvs_server_poll", "lvs_server_stats_get", "lvs_server_free",
 ]
 
@@ -54,7 +55,8 @@ class lvs_params(ctypes.Structure):
 
 
 class lvs_opts(ctypes.Structure):
-    _fields_ = [("band", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [("band", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("refresh_budget", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class lvs_query(ctypes.Structure):
@@ -128,6 +130,11 @@ def _declare(L):
         "lvs_decrypt": ([vp, vp, sz, u32p], i32),
         "lvs_decrypt_all": ([vp, vp, u32p], i32),
         "lvs_pbs_batch_device": ([vp, vp, sz, vp, vp, sz, sz], i32),
+        "lvs_pbs_batch_device_fft64": ([vp, vp, sz, vp, vp, sz, sz], i32),
+        "lvs_ctx_prepare_fft64": ([vp, vp], i32),
+        "lvs_noise_budget": ([ctypes.POINTER(lvs_params), ctypes.c_double, ctypes.POINTER(ctypes.c_double)], i32),
+        "lvs_noise_plan": ([sz, sz, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_uint8),
+                            ctypes.POINTER(ctypes.c_double)], i32),
         "lvs_keyswitch_batch_device": ([vp, vp, sz, vp, sz], i32),
         "lvs_poly_mul_device": ([vp, vp, vp, vp, sz], i32),
         "lvs_ctx_set_timing": ([vp, i32], i32),
@@ -225,11 +232,30 @@ def lvs_params_test():
     return p
 
 
-def lvs_opts_default(use_graph=True):
+def lvs_opts_default(use_graph=True, band=-1, refresh_budget=0):
+    """band >= 0: only cells with |i - j| <= band (pairs with m = n);
+    refresh_budget: 0 from the parameters, > 0 explicit, < 0 no refresh."""
     o = lvs_opts()
     lib().lvs_opts_default(ctypes.byref(o))
     o.use_graph = 1 if use_graph else 0
+    o.band = band
+    o.refresh_budget = refresh_budget
     return o
+
+
+def lvs_noise_budget(params, log2_pfail=-64.0):
+    b = ctypes.c_double()
+    _check(lib().lvs_noise_budget(ctypes.byref(params), ctypes.c_double(log2_pfail), ctypes.byref(b)))
+    return b.value
+
+
+def lvs_noise_plan(m, n, band, budget):
+    """(list of refreshed anti-diagonals d = i + j, largest key variance)."""
+    r = np.zeros(m + n + 1, dtype=np.uint8)
+    w = ctypes.c_double()
+    _check(lib().lvs_noise_plan(m, n, band, ctypes.c_double(budget),
+                                r.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.byref(w)))
+    return [int(d) for d in np.nonzero(r)[0]], w.value
 
 
 def lvs_version():
@@ -460,6 +486,15 @@ def lvs_server_stats_get(server):
 
 def lvs_pbs_batch_device(ctx, d_in, in_stride, d_lut, d_out, out_stride, count):
     _check(lib().lvs_pbs_batch_device(ctx, _ptr(d_in), in_stride, _ptr(d_lut), _ptr(d_out), out_stride, count))
+
+
+def lvs_ctx_prepare_fft64(ctx, sk):
+    _check(lib().lvs_ctx_prepare_fft64(ctx, sk))
+
+
+def lvs_pbs_batch_device_fft64(ctx, d_in, in_stride, d_lut, d_out, out_stride, count):
+    _check(lib().lvs_pbs_batch_device_fft64(ctx, _ptr(d_in), in_stride, _ptr(d_lut), _ptr(d_out), out_stride,
+                                            count))
 
 
 def lvs_pbs_batch_device_noalloc(ctx, d_in, in_stride, d_lut, d_out, out_stride, count):

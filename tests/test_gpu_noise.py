@@ -1,0 +1,107 @@
+"""Noise of the bootstrap on the GPU against the noise model of the chosen
+parameter set (the basis of the failure-probability claim; the paper's own
+accounting is Section 3.1.3 "Limiting the noise growth").
+
+For a PBS output (sample extract of the blind-rotation accumulator) the phase
+error is dominated by the gadget rounding of the external products: each CMux
+with s_i = 1 adds the rounding error of X^a ACC - ACC, uniform on
+[-2^(63-beta), 2^(63-beta)) per coefficient (beta = level * base_log),
+weighted by (1 + |S|) for the body and the mask under the binary GLWE key S.
+The bootstrapping-key noise adds n (k+1) l N E[d^2] var(TUniform(b_glwe)).
+"""
+import numpy as np
+import pytest
+
+from paper_2508_14568_gb300 import lvs as L
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def tuniform_var(b):
+    return (2.0 ** (2 * b + 1) + 1) / 6.0
+
+
+def predicted_pbs_variance(p, lwe_key, glwe_key):
+    beta = p.pbs_level * p.pbs_base_log
+    B = 2 ** p.pbs_base_log
+    rnd = (2.0 ** (63 - beta)) ** 2 / 3.0                   # uniform on [-2^(63-beta), 2^(63-beta))
+    weight = float(np.sum(lwe_key)) * (1.0 + float(np.sum(glwe_key)))
+    bsk = p.n * (p.k + 1) * p.pbs_level * p.N * (B * B / 12.0) * tuniform_var(p.glwe_noise_log2)
+    return weight * rnd + bsk
+
+
+def test_pbs_output_noise_matches_model():
+    p = L.lvs_params_default()
+    ck, sk = L.lvs_keygen(p, 5)
+    ctx = L.lvs_ctx_create(sk, 0)
+    lwe_key, glwe_key = L.lvs_client_key_export(ck)
+    big = p.k * p.N
+    count = 2048
+    rng = np.random.default_rng(1)
+    msgs = rng.integers(0, 16, size=count)
+    cts = np.stack([L.lvs_encrypt_lwe(ck, int(m), 8, 0, i, big) for i, m in enumerate(msgs)])
+    ident = np.tile(np.arange(16, dtype=np.uint8), (count, 1))          # f(x) = x
+    d_in = torch.from_numpy(cts.view(np.int64)).cuda()
+    d_out = torch.zeros_like(d_in)
+    L.lvs_pbs_batch_device(ctx, d_in, big + 1, torch.from_numpy(ident).cuda(), d_out, big + 1, count)
+    L.lvs_ctx_synchronize(ctx)
+    out = d_out.cpu().numpy().view(np.uint64)
+    mask = glwe_key.astype(bool)
+    phase = out[:, big] - out[:, :big][:, mask].sum(axis=1, dtype=np.uint64)
+    err = (phase - (msgs.astype(np.uint64) << np.uint64(59))).view(np.int64).astype(np.float64)
+    measured = float(np.mean(err ** 2))
+    predicted = predicted_pbs_variance(p, lwe_key, glwe_key)
+    ratio = measured / predicted
+    print("PBS noise: measured 2^%.3f predicted 2^%.3f ratio %.3f" % (np.log2(measured), np.log2(predicted), ratio))
+    assert abs(float(np.mean(err))) < 4 * np.sqrt(measured / count)
+    assert 0.85 < ratio < 1.15
+    # every output decrypts (margin 2^58 = many standard deviations)
+    assert np.max(np.abs(err)) < 2.0 ** 58
+
+
+def test_failure_rate_of_increasingly_noisy_ciphertexts():
+    """Section 3.1.3's experiment: bootstrap ciphertexts carrying more and
+    more accumulated noise and count decoding errors.  An input
+    m + c * Z (Z a fresh PBS output of 0, so the added variance is c^2 times
+    that of a PBS output) is bootstrapped with the identity table; the error
+    count must follow the failure probability of the noise model (normal
+    tail of the key, key-switch and modulus-switch variances)."""
+    from oracle import noise as Nz
+    from oracle import tfhe as T
+
+    p = L.lvs_params_default()
+    pd = T.params_lvs().as_dict()
+    ck, sk = L.lvs_keygen(p, 9)
+    ctx = L.lvs_ctx_create(sk, 0)
+    big = p.k * p.N
+    count = 4096
+    rng = np.random.default_rng(4)
+    ident = torch.from_numpy(np.tile(np.arange(16, dtype=np.uint8), (count, 1))).cuda()
+
+    def pbs(cts):
+        d_in = torch.from_numpy(np.ascontiguousarray(cts).view(np.int64)).cuda()
+        d_out = torch.zeros_like(d_in)
+        L.lvs_pbs_batch_device(ctx, d_in, big + 1, ident, d_out, big + 1, cts.shape[0])
+        L.lvs_ctx_synchronize(ctx)
+        return d_out.cpu().numpy().view(np.uint64).copy()
+
+    zeros = pbs(np.stack([L.lvs_encrypt_lwe(ck, 0, 10, 0, i, big) for i in range(count)]))
+    msgs = rng.integers(0, 16, size=count)
+    fresh = pbs(np.stack([L.lvs_encrypt_lwe(ck, int(m), 11, 0, i, big) for i, m in enumerate(msgs)]))
+    rows = []
+    for c in (1200, 1800, 2400, 3000):
+        noisy = fresh + np.uint64(c) * zeros
+        out = pbs(noisy)
+        got = np.array([L.lvs_decrypt_lwe(ck, r) for r in out])
+        errors = int(np.sum(got != msgs))
+        pred = Nz.pfail_of(pd, 1 + c * c)
+        expect = pred * count
+        rows.append((c, errors, expect))
+        print("c = %d: key variance %d PBS units, %d errors, predicted %.1f" % (c, 1 + c * c, errors, expect))
+        # binomial agreement: 5 sigma plus 20 % model slack
+        assert abs(errors - expect) <= 5 * np.sqrt(expect + 1) + 0.2 * expect
+    # errors grow with the noise
+    assert rows[-1][1] > rows[0][1]
+    L.lvs_ctx_free(ctx)
