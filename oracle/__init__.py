@@ -9,7 +9,7 @@ Modules
 -------
 ``plain``   plaintext algorithms: Wagner-Fischer (Eq. eq_wf), a breadth-first
             search over single edit operations (the definition of the edit
-            distance in Section 2.3), the Myers cell equations (Section 2.3.4),
+            distance in Section 2.3), the Myers cell equations (Section 2.3.3),
             the Leuvenshtein one-lookup cell (Eq. mye_eq_2, Eq. eq_keyeq2,
             Table LUTmin), the ASCII two-lookup equality (Algorithm alg_ascii),
             the preprocessing table (Section 5, Table tab_pre) and PBS counts

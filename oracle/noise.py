@@ -18,6 +18,8 @@ are refreshed by a bootstrap, which makes them fresh independent units.
 """
 import math
 
+from .plain import in_band
+
 
 class _Tracker:
     """Linear combinations over independent unit-variance noises."""
@@ -42,10 +44,6 @@ class _Tracker:
         return sum(a * a for a in x.values())
 
 
-def in_band(i, j, band):
-    return band is None or abs(i - j) <= band
-
-
 def key_variances(m, n, band=None, refresh=frozenset()):
     """Variances (eps^2_PBS units) of the key of every computed cell (i, j)
     and of its swapped key (1 - dh_in) + 3 (1 + dv_in) + EQ9, which a
@@ -63,7 +61,7 @@ def key_variances(m, n, band=None, refresh=frozenset()):
     for d in range(2, m + n + 1):
         for i in range(max(1, d - n), min(m, d - 1) + 1):
             j = d - i
-            if not in_band(i, j, band):
+            if not in_band(i, j, m, n, band):
                 continue
             dv_in = v.get((i, j - 1), zero)
             dh_in = h.get((i - 1, j), zero)

@@ -103,7 +103,7 @@ def deltas_from_matrix(D):
 
 
 def myers_cell(dv_in, dh_in, eq):
-    """The cell equations of Section 2.3.4 (Myers):
+    """The cell equations of Section 2.3.3 (Myers):
     dv_out = min(1, dv_in + 1 - dh_in, 1 - eq - dh_in),
     dh_out = min(1, 1 + dh_in - dv_in, 1 - eq - dv_in)."""
     dv_out = min(1, dv_in + 1 - dh_in, 1 - eq - dh_in)
@@ -310,15 +310,28 @@ def lvs_plain(a, b, alphabet=ALPHA_ASCII7):
     return dist, h, v, lookups
 
 
+def in_band(i, j, m, n, band):
+    """The band of Section 3.2 (Algorithm alg_levenshtein: |i - j| <= band for
+    m = n), widened for m != n to the diagonals k = j - i with
+    min(0, n - m) - band <= k <= max(0, n - m) + band: the cells with
+    |k| + |(n - m) - k| <= |n - m| + 2 band, where every edit path of cost at
+    most |n - m| + 2 band lies (a path through diagonal k costs at least |k| to
+    get there and |n - m - k| to get back).  band None: every cell."""
+    if band is None:
+        return True
+    k, delta = j - i, n - m
+    return min(0, delta) - band <= k <= max(0, delta) + band
+
+
 def lvs_on_eq9(E9, m, n, band=None):
     """Algorithm alg_levenshtein on a given EQ9 matrix (E9[i][j] in {0, 9},
-    1-based), with optional band |i - j| <= band.  Out-of-band cells keep the
+    1-based), with optional band (in_band).  Out-of-band cells keep the
     OneMatrix value 1.  Returns (h, v) in Z_32."""
     h = [[1] * (n + 1) for _ in range(m + 1)]
     v = [[1] * (n + 1) for _ in range(m + 1)]
     for j in range(1, n + 1):
         for i in range(1, m + 1):
-            if band is not None and abs(i - j) > band:
+            if not in_band(i, j, m, n, band):
                 continue
             key = ((1 - v[i][j - 1]) + 3 * (1 + h[i - 1][j]) + E9[i][j]) % PLAIN_MOD
             M = lookup(LUT_MIN, key)
@@ -335,6 +348,29 @@ def readout_row(h, m, n):
 def readout_diagonal(h, v, m):
     """Square band readout (Section 3.2): D[m][m] = sum_{i=1..m} (v[i][i-1] + h[i][i])."""
     return sum(signed(v[i][i - 1]) + signed(h[i][i]) for i in range(1, m + 1))
+
+
+def readout_path_cells(m, n):
+    """The monotone path of the band readout from (0, 0) to (m, n): down the
+    main diagonal (v[i][i-1], then h[i][i]) for i <= min(m, n), then along row
+    m (h[m][j], j > m) or down column n (v[i][n], i > n).  For band >= 1
+    every step is a boundary value or a cell inside the band (band 0 leaves
+    the v[i][i-1] at their OneMatrix value).  Returns [(i, j, 'v' | 'h')]:
+    D[m][n] is the sum."""
+    r = min(m, n)
+    path = []
+    for i in range(1, r + 1):
+        path += [(i, i - 1, "v"), (i, i, "h")]
+    if n > m:
+        path += [(m, j, "h") for j in range(m + 1, n + 1)]
+    else:
+        path += [(i, n, "v") for i in range(n + 1, m + 1)]
+    return path
+
+
+def readout_path(h, v, m, n):
+    """D[m][n] as the sum of the differences along readout_path_cells."""
+    return sum(signed((v if s == "v" else h)[i][j]) for i, j, s in readout_path_cells(m, n))
 
 
 # ---------------------------------------------------------------------------
@@ -371,6 +407,11 @@ def lvs_preprocessed_plain(table, plain_b, m):
 def pbs_count_exact(m, n, eq_per_cell=2):
     """Table tab_pbs, Leuvenshtein Exact: (eq lookups + 1) per cell."""
     return (eq_per_cell + 1) * m * n
+
+
+def band_cells_general(m, n, band):
+    """Cells of an m x n matrix inside in_band."""
+    return sum(1 for i in range(1, m + 1) for j in range(1, n + 1) if in_band(i, j, m, n, band))
 
 
 def band_cells(m, band):

@@ -313,8 +313,8 @@ def encrypt_string(keys, s, alphabet, noise_seed, string_id):
 
 def lvs_encrypted(keys, xa, yb, alphabet, parallel=False, band=None, refresh=()):
     """Algorithm algo_complete on ciphertexts (with ``band``: only the cells
-    with |i - j| <= band, the condition of Algorithm alg_levenshtein; the
-    others keep the OneMatrix value 1).
+    inside plain.in_band -- |i - j| <= band for m = n, the condition of
+    Algorithm alg_levenshtein; the others keep the OneMatrix value 1).
 
     ``refresh``: anti-diagonals d = i + j whose dv, dh are refreshed by a
     bootstrap (Section 3.1.3): such a cell takes two lookups through LUT_V,
@@ -338,7 +338,8 @@ def lvs_encrypted(keys, xa, yb, alphabet, parallel=False, band=None, refresh=())
     Returns a dict with the PBS outputs per cell ('eq1', 'eq9', 'M'), the
     final row h[m][1..n] ('h_row'), the final column v[1..m][n] ('v_col'),
     for square pairs the diagonal path [v[1][0], h[1][1], ..., v[m][m-1],
-    h[m][m]] ('diag', the readout of Section 3.2) and the number of PBS.
+    h[m][m]] ('diag', the readout of Section 3.2), the band readout path of
+    plain.readout_path_cells ('path') and the number of PBS.
     """
     m, n = len(xa), len(yb)
     one = trivial(keys, 1)
@@ -355,7 +356,7 @@ def lvs_encrypted(keys, xa, yb, alphabet, parallel=False, band=None, refresh=())
         return scalar(2, xa[i - 1][1] - yb[j - 1][1]) + (one - e1)
 
     def inside(i, j):
-        return band is None or abs(i - j) <= band
+        return P.in_band(i, j, m, n, band)
 
     def key_of(i, j):
         return (one - v.get((i, j - 1), one)) + scalar(3, one + h.get((i - 1, j), one)) + res["eq9"][(i, j)]
@@ -419,6 +420,7 @@ def lvs_encrypted(keys, xa, yb, alphabet, parallel=False, band=None, refresh=())
     res["v_col"] = [v.get((i, n), one) for i in range(1, m + 1)]
     if m == n:
         res["diag"] = [c for i in range(1, m + 1) for c in (v.get((i, i - 1), one), h.get((i, i), one))]
+    res["path"] = [(v if s == "v" else h).get((i, j), one) for i, j, s in P.readout_path_cells(m, n)]
     res["pbs"] = npbs
     return res
 

@@ -242,3 +242,53 @@ def test_preprocessed_plain_equals_wf():
         b = "".join(rng.choice(pool) for _ in range(rng.randint(1, 12)))
         t = P.preprocess_table(a, pool, P.ALPHA_27)
         assert P.lvs_preprocessed_plain(t, b, len(a)) == P.wf_distance(a, b)
+
+
+def _e9(a, b):
+    m, n = len(a), len(b)
+    return [[9 if i and j and a[i - 1] == b[j - 1] else 0 for j in range(n + 1)] for i in range(m + 1)]
+
+
+def test_general_band_reduces_to_square_band():
+    for m in range(1, 9):
+        for band in range(0, m + 1):
+            for i in range(1, m + 1):
+                for j in range(1, m + 1):
+                    assert P.in_band(i, j, m, m, band) == (abs(i - j) <= band)
+    assert P.band_cells_general(7, 7, 2) == P.band_cells(7, 2)
+
+
+def test_readout_path_is_monotone_inside_bands_from_1():
+    for m in range(0, 7):
+        for n in range(0, 7):
+            path = P.readout_path_cells(m, n)
+            assert len(path) == m + n
+            pos = (0, 0)
+            for i, j, s in path:
+                # one step down (v) or right (h)
+                assert (i, j) == ((pos[0] + 1, pos[1]) if s == "v" else (pos[0], pos[1] + 1))
+                pos = (i, j)
+                assert j == 0 or P.in_band(i, j, m, n, 1)
+            assert pos == (m, n)
+
+
+def test_non_square_band_exact_and_upper_bound():
+    """Ukkonen's argument: an edit path through diagonal k = j - i costs at
+    least |k| + |(n - m) - k|, so with band >= ceil(min(m, n) / 2) every
+    optimal path lies in the band and the readout is exact; narrower bands
+    are exact whenever D <= |n - m| + 2 band and never below D."""
+    rng = random.Random(11)
+    for _ in range(1500):
+        m, n = rng.randint(1, 9), rng.randint(1, 9)
+        a = "".join(rng.choice("abc") for _ in range(m))
+        b = "".join(rng.choice("abc") for _ in range(n))
+        wf = P.wf_distance(a, b)
+        E9 = _e9(a, b)
+        h, v = P.lvs_on_eq9(E9, m, n, (min(m, n) + 1) // 2)
+        assert P.readout_path(h, v, m, n) == wf
+        band = rng.randint(0, max(m, n))
+        h, v = P.lvs_on_eq9(E9, m, n, band)
+        d = P.readout_path(h, v, m, n)
+        assert d >= wf
+        if wf <= abs(n - m) + 2 * band:
+            assert d == wf
