@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=None, help="PBS in the oracle sample (default: host cores)")
+    ap.add_argument("--pbs-variants", type=int, default=0, metavar="COUNT",
+                    help="instead of a config: time COUNT independent PBS through the exact NTT blind rotation "
+                         "and through the FP64-FFT one (side measurement, its own JSON line)")
     return ap.parse_args()
 
 
@@ -270,7 +273,11 @@ def run_lvs(args):
     A_L = {"ascii7": L.LVS_ALPHA_ASCII7, "alpha27": L.LVS_ALPHA_27, "dna4": L.LVS_ALPHA_DNA4}[alpha]
     params = L.lvs_params_default()
     ck, sk = L.lvs_keygen(params, 0)
-    stream = torch.cuda.current_stream()
+    # a stream of our own: the library runs on it and the timing events are
+    # recorded on it (the default stream has handle 0, which the library reads
+    # as "no stream given" and replaces with a non-blocking stream of its own)
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
     ctx = L.lvs_ctx_create(sk, local, stream)
     big = params.k * params.N
     cells = sum(len(a) * len(b) for a, b in pairs)
@@ -333,13 +340,17 @@ def run_lvs(args):
     pbs_all = sum_over_ranks(pbs_done)
     value = cells_all / t_max
 
-    # roofline of the blind-rotation kernel (ALU bound: 32-bit multiplies)
+    # roofline of the blind-rotation kernel (ALU bound: modular multiplications)
     w_mod = modmul_per_pbs(params)
     avg_launch_s = br["total_ms"] / max(1, br["launches"]) / 1e3
     units_per_launch = br["items"] / max(1, br["launches"])
-    achieved = 3 * w_mod * units_per_launch / avg_launch_s / 1e12 if br["launches"] else None
+    achieved = w_mod * units_per_launch / avg_launch_s / 1e12 if br["launches"] else None
     sm_mhz_max = clk.get("sm_max_mhz") or 2070.0
-    peak = SM_COUNT_NOMINAL * MUL32_PER_SM_CLK * sm_mhz_max * 1e6 / 1e12
+    mul_lo, mul_hi = L.lvs_probe_int_mul(local)
+    modmul_per_sm_clk = 1.0 / (2.0 / mul_lo + 1.0 / mul_hi)
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = n_sms * modmul_per_sm_clk * sm_mhz_max * 1e6 / 1e12
+    peak_mul32 = n_sms * MUL32_PER_SM_CLK * sm_mhz_max * 1e6 / 1e12
     trec = traffic_record()
     traffic = None
     if trec:
@@ -432,13 +443,17 @@ def run_lvs(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "pbs_per_s": pbs_all / t_max,
             "gpu_launches": launches,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmul32/s",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tmodmul/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "kernel": "k_blind_rotate<11>",
                          "units_per_launch": units_per_launch, "launch_ms": avg_launch_s * 1e3,
-                         "mul32_per_pbs": 3 * w_mod,
-                         "peak_note": "%d SMs x %d int32 mul/clk x max SM clock (derived)" % (
-                             SM_COUNT_NOMINAL, MUL32_PER_SM_CLK)},
+                         "modmul_per_pbs": w_mod,
+                         "peak_note": "%d SMs x %.1f modmul/SM/clk x max SM clock %.0f MHz; a Shoup modmul = 2 "
+                                      "low + 1 high 32-bit multiplies at the measured issue rates (lo %.1f, hi %.1f "
+                                      "per SM per clk, lvs_probe_int_mul)" % (
+                                          n_sms, modmul_per_sm_clk, sm_mhz_max, mul_lo, mul_hi),
+                         "frac_all_mul_at_lo_rate": (3 * w_mod * units_per_launch / avg_launch_s / 1e12 / peak_mul32)
+                         if achieved else None},
             "kernels": {"blind_rotate": br, "keyswitch": ks},
             "latency_ms": {"p50": batched_latency_ms, "p99": batched_latency_ms,
                            "note": "batched: all pairs of a step complete together"},
@@ -511,10 +526,57 @@ def run_serving(args):
     return 0
 
 
+def run_pbs_variants(args):
+    """PBS/s of the two blind-rotation variants on one batch of independent
+    PBS at the default parameters (inputs resident on the device, identity
+    table), with a decryption check of every output."""
+    import numpy as np
+    import torch
+    from paper_2508_14568_gb300 import lvs as L
+    params = L.lvs_params_default()
+    ck, sk = L.lvs_keygen(params, 0)
+    stream = torch.cuda.Stream(device=0)
+    torch.cuda.set_stream(stream)
+    ctx = L.lvs_ctx_create(sk, 0, stream)
+    L.lvs_ctx_prepare_fft64(ctx, sk)
+    big = params.k * params.N
+    count = args.pbs_variants
+    msgs = np.arange(count) % 16
+    cts = np.stack([L.lvs_encrypt_lwe(ck, int(m), 3, 0, i, big) for i, m in enumerate(msgs)])
+    d_in = torch.from_numpy(cts.view(np.int64)).cuda()
+    d_out = torch.zeros_like(d_in)
+    luts = torch.from_numpy(np.tile(np.arange(16, dtype=np.uint8), (count, 1))).cuda()
+    line = {"metric": "PBS/s by blind-rotation variant", "unit": "PBS/s", "count": count,
+            "steps": args.steps, "warmup": args.warmup,
+            "params": "n=834 k=1 N=2048 pbs 2x2^13 ks 5x2^3", "variants": {}}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name, fn in (("ntt_exact", L.lvs_pbs_batch_device), ("fft64", L.lvs_pbs_batch_device_fft64)):
+        for _ in range(max(1, args.warmup)):
+            fn(ctx, d_in, big + 1, luts, d_out, big + 1, count)
+        torch.cuda.synchronize()
+        got = [L.lvs_decrypt_lwe(ck, r) for r in d_out.cpu().numpy().view(np.uint64)]
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            fn(ctx, d_in, big + 1, luts, d_out, big + 1, count)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        line["variants"][name] = {"value": count / (ms * 1e-3), "ms_per_batch": ms,
+                                  "decrypt_ok": bool(np.array_equal(np.array(got), msgs))}
+    line["clocks"] = clocks.stop()
+    L.lvs_ctx_free(ctx)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.pbs_variants:
+        return run_pbs_variants(args)
     if args.config == 5:
         return run_serving(args)
     return run_lvs(args)

@@ -161,10 +161,15 @@ lvs_status lvs_encrypt_lwe(const lvs_client_key *ck, uint32_t value, uint64_t no
  * this library compute every cell). */
 typedef struct lvs_opts {
     int32_t band;          /* < 0: full matrix.  >= 0: only the cells with      *
-                            * |i - j| <= band (Algorithm alg_levenshtein), for   *
-                            * pairs with m = n; band = floor(m/2) is exact       *
-                            * ("Exact Skip", Section 3.2), smaller bands give    *
-                            * the approximate distance of Section 3.2            */
+                            * |i - j| <= band for m = n (Algorithm               *
+                            * alg_levenshtein; band = floor(m/2) is exact,       *
+                            * "Exact Skip", Section 3.2); for m != n the         *
+                            * diagonals k = j - i with min(0, n-m) - band <= k   *
+                            * <= max(0, n-m) + band, where every edit path of    *
+                            * cost <= |n-m| + 2 band lies (exact for band >=     *
+                            * ceil(min(m,n)/2)).  Narrower bands give the        *
+                            * approximate distance of Section 3.2 (never below   *
+                            * the true distance)                                 */
     int32_t use_graph;     /* 1: capture the wavefront launches in a CUDA graph  */
     int32_t refresh_budget;/* noise budget of a key, in units of the variance   *
                             * of a fresh PBS output (Section 3.1.3; the paper's  *
@@ -185,8 +190,8 @@ void lvs_opts_default(lvs_opts *o);
  * of expected weight) decodes wrongly with probability at most 2^log2_pfail
  * (log2_pfail < 0).  Host only. */
 lvs_status lvs_noise_budget(const lvs_params *p, double log2_pfail, double *budget);
-/* Refresh plan of one m x n difference matrix (band < 0: full; else cells
- * with |i - j| <= band).  Each M and EQ9 is a unit noise, dv_out = M - dh_in,
+/* Refresh plan of one m x n difference matrix (band < 0: full; else the
+ * cells of lvs_opts.band).  Each M and EQ9 is a unit noise, dv_out = M - dh_in,
  * dh_out = M - dv_in; a cell costs the larger variance of its key and of its
  * key with dv_in, dh_in exchanged.  An anti-diagonal d = i + j is refreshed
  * when, without it, a cell of d + 1 would cost more than budget (budget <= 0:
@@ -209,9 +214,11 @@ lvs_status lvs_eq(lvs_ctx *ctx, const lvs_ct_string *a, size_t i, const lvs_ct_s
  * s-1, EQ1 of s} (Section 6.2 "Parallelism": cells of one anti-diagonal are
  * independent).  The result holds, per pair, the encrypted last row
  * h[m][1..n] and the plaintext m; the distance is m + sum_j dec(h[m][j]).
- * With a band (opts->band >= 0) the result holds instead the diagonal path
- * [v[1][0], h[1][1], ..., v[m][m-1], h[m][m]] (2m ciphertexts) and the
- * distance is its decrypted sum (Section 3.2 readout).
+ * With a band (opts->band >= 0) the result holds instead the m + n
+ * differences along a monotone path from (0, 0) to (m, n): [v[1][0], h[1][1],
+ * ..., v[r][r-1], h[r][r]] (r = min(m, n), the diagonal readout of Section
+ * 3.2), then h[m][m+1..n] or v[r+1..m][n]; the distance is their decrypted
+ * sum.
  * Both strings of a pair must share the alphabet; lengths may be 0. */
 lvs_status lvs_edit_distance_batch(lvs_ctx *ctx, const lvs_ct_string *const *a,
                                    const lvs_ct_string *const *b, size_t npairs,
@@ -346,6 +353,29 @@ lvs_status lvs_pbs_batch_device_fft64(lvs_ctx *ctx, const uint64_t *d_in, size_t
 lvs_status lvs_pbs_batch_device_noalloc(lvs_ctx *ctx, const uint64_t *d_in, size_t in_stride,
                                         const uint8_t *d_lut, uint64_t *d_out, size_t out_stride,
                                         size_t count);
+
+/* Autotuner of the key-switch launch shape (no counterpart in the paper):
+ * for each launch-size bucket (1-4, 5-16, 17-64, 65-256, 257-1024, more
+ * PBS per launch) it times every candidate plan -- 4 or 16 PBS per CTA,
+ * the 2048 input coefficients split over 1..32 CTAs with a finishing
+ * reduction -- on synthetic jobs and keeps the fastest in the context.
+ * Without it a heuristic plan is used (fill about two CTAs per SM).  Every
+ * plan gives the same result bit for bit.  Synchronous; takes about a second;
+ * allocates and frees its own scratch. */
+lvs_status lvs_ctx_autotune(lvs_ctx *ctx);
+/* The plan used for a launch of njobs PBS (jobs per CTA, split). */
+lvs_status lvs_ctx_ks_plan(lvs_ctx *ctx, size_t njobs, int32_t *jobs_per_cta, int32_t *split);
+/* Forces the plan of njobs' bucket (jobs_per_cta 4 or 16, split 1..32;
+ * jobs_per_cta 0 restores the heuristic).  For tests and experiments. */
+lvs_status lvs_ctx_set_ks_plan(lvs_ctx *ctx, size_t njobs, int32_t jobs_per_cta, int32_t split);
+
+/* Measured issue rate of 32-bit integer multiplies on `device`: low-half
+ * (mul.lo / IMAD) and high-half (mul.hi) results per SM per clock, from one
+ * CTA per SM timed with the SM clock counter.  The roofline of the blind
+ * rotation (no counterpart in the paper) uses it: a word-size modular
+ * multiplication by a constant (Shoup) costs two low-half and one high-half
+ * multiply.  Synchronous; allocates and frees its own buffers. */
+lvs_status lvs_probe_int_mul(int device, double *lo_per_sm_clk, double *hi_per_sm_clk);
 
 /* Key switch + modulus switch only: d_out receives count * (n+1) uint32
  * values round(a * 2N / 2^64) of the key-switched ciphertexts. */

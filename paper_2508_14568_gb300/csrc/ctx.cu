@@ -36,6 +36,21 @@ lvs_status ensure_scratch(lvs_ctx *ctx, size_t njobs_total, size_t njobs_step)
         }
         ctx->jobs_cap = cap;
     }
+    // split key-switch scratch: the largest need over launch sizes up to njobs_step
+    // (the plan is constant within a bucket, so bucket ends and njobs_step suffice)
+    size_t part = 0;
+    for (size_t lim = 4; lim < njobs_step; lim *= 4) part = std::max(part, ks_part_words(ctx, lim));
+    if (njobs_step) part = std::max(part, ks_part_words(ctx, njobs_step));
+    if (part > ctx->ks_part_cap) {
+        if (ctx->ks_part) LVS_CUDA(cudaFreeAsync(ctx->ks_part, ctx->stream));
+        ctx->ks_part = nullptr;
+        ctx->ks_part_cap = 0;
+        if (cudaMallocAsync((void **)&ctx->ks_part, part * sizeof(uint64_t), ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(LVS_ERR_OOM, "device allocation of the key-switch partial sums failed");
+        }
+        ctx->ks_part_cap = part;
+    }
     if (njobs_step > ctx->ms_cap) {
         if (ctx->ms) LVS_CUDA(cudaFreeAsync(ctx->ms, ctx->stream));
         ctx->ms = nullptr;
@@ -110,14 +125,15 @@ static lvs_status launch_step(lvs_ctx *ctx, const Job *d_jobs, size_t nj, bool t
         if (!a || !b || !c) return set_error(LVS_ERR_CUDA, "event creation failed");
         LVS_CUDA(cudaEventRecord(a, ctx->stream));
     }
-    LVS_CUDA(launch_keyswitch(ctx, d_jobs, nj, ctx->ms, ctx->stream));
+    int nks = 0;
+    LVS_CUDA(launch_keyswitch(ctx, d_jobs, nj, ctx->ms, ctx->stream, &nks));
     if (timed) LVS_CUDA(cudaEventRecord(b, ctx->stream));
     LVS_CUDA(launch_blind_rotate(ctx, d_jobs, nj, ctx->ms, ctx->luts, 0, ctx->stream));
     if (timed) {
         LVS_CUDA(cudaEventRecord(c, ctx->stream));
         ctx->timing.pending.push_back({a, b, c, nj});
     }
-    ctx->launches += 2;
+    ctx->launches += nks + 1;
     return LVS_OK;
 }
 
@@ -248,6 +264,7 @@ void lvs_ctx_free(lvs_ctx *ctx)
     cudaFree(ctx->fft_tw);
     if (ctx->ms) cudaFree(ctx->ms);
     if (ctx->jobs) cudaFree(ctx->jobs);
+    if (ctx->ks_part) cudaFree(ctx->ks_part);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     cudaGetLastError();
     delete ctx;
@@ -329,7 +346,8 @@ lvs_status lvs_pbs_batch_device(lvs_ctx *ctx, const uint64_t *d_in, size_t in_st
             if (!a || !b || !c) return set_error(LVS_ERR_CUDA, "event creation failed");
             LVS_CUDA(cudaEventRecord(a, ctx->stream));
         }
-        LVS_CUDA(launch_keyswitch(ctx, ctx->jobs, nc, ctx->ms, ctx->stream));
+        int nks = 0;
+        LVS_CUDA(launch_keyswitch(ctx, ctx->jobs, nc, ctx->ms, ctx->stream, &nks));
         if (timed) LVS_CUDA(cudaEventRecord(b, ctx->stream));
         LVS_CUDA(launch_blind_rotate(ctx, ctx->jobs, nc, ctx->ms, d_lut + c0 * 16, 1, ctx->stream));
         if (timed) {
@@ -337,7 +355,7 @@ lvs_status lvs_pbs_batch_device(lvs_ctx *ctx, const uint64_t *d_in, size_t in_st
             ctx->timing.pending.push_back({a, b, c, nc});
         }
         ctx->pbs_done += nc;
-        ctx->launches += 2;
+        ctx->launches += nks + 1;
     }
     return LVS_OK;
 }
@@ -355,11 +373,12 @@ lvs_status lvs_keyswitch_batch_device(lvs_ctx *ctx, const uint64_t *d_in, size_t
         jobs[i].src[0] = d_in + i * in_stride;
         jobs[i].coef[0] = 1;
     }
-    lvs_status st = ensure_scratch(ctx, count, 0);
+    lvs_status st = ensure_scratch(ctx, count, count);
     if (st != LVS_OK) return st;
     LVS_CUDA(cudaMemcpyAsync(ctx->jobs, jobs.data(), count * sizeof(Job), cudaMemcpyHostToDevice, ctx->stream));
-    LVS_CUDA(launch_keyswitch(ctx, ctx->jobs, count, d_out, ctx->stream));
-    ctx->launches += 1;
+    int nks = 0;
+    LVS_CUDA(launch_keyswitch(ctx, ctx->jobs, count, d_out, ctx->stream, &nks));
+    ctx->launches += nks;
     return LVS_OK;
 }
 

@@ -338,7 +338,8 @@ lvs_status lvs_pbs_batch_device_fft64(lvs_ctx *ctx, const uint64_t *d_in, size_t
         lvs_status st = ensure_scratch(ctx, nc, nc);
         if (st != LVS_OK) return st;
         LVS_CUDA(cudaMemcpyAsync(ctx->jobs, jobs.data(), nc * sizeof(Job), cudaMemcpyHostToDevice, ctx->stream));
-        LVS_CUDA(launch_keyswitch(ctx, ctx->jobs, nc, ctx->ms, ctx->stream));
+        int nks = 0;
+        LVS_CUDA(launch_keyswitch(ctx, ctx->jobs, nc, ctx->ms, ctx->stream, &nks));
         const unsigned grid = (unsigned)std::min<size_t>(nc, (size_t)ctx->fft_grid);
         if (p.N == 2048)
             fft::k_blind_rotate_fft<11><<<grid, fft::kThreads, fft::FftSmem<11>::total, ctx->stream>>>(
@@ -348,7 +349,7 @@ lvs_status lvs_pbs_batch_device_fft64(lvs_ctx *ctx, const uint64_t *d_in, size_t
                 ctx->jobs, (uint32_t)nc, ctx->ms, p.n, bsk, t2, ts2, d_lut + c0 * 16, 1, p.pbs_base_log);
         LVS_CUDA(cudaGetLastError());
         ctx->pbs_done += nc;
-        ctx->launches += 2;
+        ctx->launches += nks + 1;
     }
     return LVS_OK;
 }

@@ -64,15 +64,18 @@ __device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][16], const uin
             na = __ldg(np);
             nb = __ldg(np + 1);
         }
-        const uint32_t d0 = csub(csub(d[0][q], 2 * p), p);
-        const uint32_t d1 = csub(csub(d[1][q], 2 * p), p);
-        const uint32_t d2 = csub(csub(d[2][q], 2 * p), p);
-        const uint32_t d3 = csub(csub(d[3][q], 2 * p), p);
+        // transform values in [0, 4p) -> [0, 2p); key residues < p: each sum of
+        // four products is below 8 p^2 < 2^63, REDC returns it below 3p, and one
+        // more conditional subtraction gives the [0, 2p) the inverse expects
+        const uint32_t d0 = csub(d[0][q], 2 * p);
+        const uint32_t d1 = csub(d[1][q], 2 * p);
+        const uint32_t d2 = csub(d[2][q], 2 * p);
+        const uint32_t d3 = csub(d[3][q], 2 * p);
         // slot = row * 2 + column
         const uint64_t t0 = (uint64_t)d0 * ka.x + (uint64_t)d1 * ka.z + (uint64_t)d2 * kb.x + (uint64_t)d3 * kb.z;
         const uint64_t t1 = (uint64_t)d0 * ka.y + (uint64_t)d1 * ka.w + (uint64_t)d2 * kb.y + (uint64_t)d3 * kb.w;
-        d[0][q] = redc(t0, p, pinv);
-        d[1][q] = redc(t1, p, pinv);
+        d[0][q] = csub(redc(t0, p, pinv), 2 * p);
+        d[1][q] = csub(redc(t1, p, pinv), 2 * p);
         if (q + 1 < 16) { ka = na; kb = nb; }
     }
     ntt_inverse2<LOGN>(d, reinterpret_cast<uint2 *>(buf), tau, twi, p, 1 + g);
@@ -204,22 +207,28 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
 // KSK word go through one 32x32->64 multiply-add into a 64-bit sum and the high
 // 32 bits through one 32-bit multiply-add (only needed mod 2^32); the offset
 // comes back as (B/2) * colsum[c], colsum[c] = sum_{u,lev} KSK[u][lev][c].
-constexpr int KS_TJ = 16;       // jobs per CTA
 constexpr int KS_THREADS = 128; // output columns per CTA
 constexpr int KS_UCH = 64;      // input coefficients per digit chunk
 constexpr int KS_MAXL = 8;
 
+// TJ jobs per CTA (a multiple of 4).  blockIdx.z / gridDim.z splits the input
+// coefficients into chunk ranges ("split-K"): with one split the epilogue adds
+// the body and modulus-switches into ms; with several, each split writes its
+// partial sum (mod 2^64, offset not yet removed) to part[z][j][c] and
+// k_ks_finish completes them.
+template <int TJ>
 __global__ void __launch_bounds__(KS_THREADS)
 k_keyswitch(const Job *__restrict__ jobs, uint32_t njobs,
             const uint64_t *__restrict__ ksk, const uint64_t *__restrict__ colsum, uint32_t n, uint32_t big,
-            uint32_t ks_level, uint32_t ks_base_log, uint32_t log2_2N, uint32_t *__restrict__ ms)
+            uint32_t ks_level, uint32_t ks_base_log, uint32_t log2_2N, uint32_t *__restrict__ ms,
+            uint64_t *__restrict__ part)
 {
-    __shared__ __align__(16) uint32_t dig[KS_UCH][KS_MAXL][KS_TJ];
-    __shared__ Job sj[KS_TJ];
+    __shared__ __align__(16) uint32_t dig[KS_UCH][KS_MAXL][TJ];
+    __shared__ Job sj[TJ];
     const int t = threadIdx.x;
-    const uint32_t j0 = blockIdx.x * KS_TJ;
+    const uint32_t j0 = blockIdx.x * TJ;
     const uint32_t c = blockIdx.y * KS_THREADS + t;
-    if (t < KS_TJ) {
+    if (t < TJ) {
         if (j0 + t < njobs) sj[t] = jobs[j0 + t];
         else {
             Job z{};
@@ -231,17 +240,21 @@ k_keyswitch(const Job *__restrict__ jobs, uint32_t njobs,
     const uint32_t beta = ks_level * ks_base_log;
     const uint64_t rnd = 1ull << (63 - beta);
     const uint32_t Bk = 1u << ks_base_log, hBk = Bk >> 1;
-    uint64_t lo[KS_TJ];
-    uint32_t hi[KS_TJ];
+    uint64_t lo[TJ];
+    uint32_t hi[TJ];
 #pragma unroll
-    for (int jj = 0; jj < KS_TJ; ++jj) { lo[jj] = 0; hi[jj] = 0; }
+    for (int jj = 0; jj < TJ; ++jj) { lo[jj] = 0; hi[jj] = 0; }
 
-    // digit prologue: thread t covers coefficient u0 + (t % KS_UCH) of 8 jobs
-    const int tu = t % KS_UCH, tj = (t / KS_UCH) * (KS_TJ / 2);
-    for (uint32_t u0 = 0; u0 < big; u0 += KS_UCH) {
+    // this split's chunk range
+    const uint32_t nch = (big + KS_UCH - 1) / KS_UCH, S = gridDim.z, z = blockIdx.z;
+    const uint32_t ch0 = (uint32_t)(((uint64_t)nch * z) / S), ch1 = (uint32_t)(((uint64_t)nch * (z + 1)) / S);
+
+    // digit prologue: thread t covers coefficient u0 + (t % KS_UCH) of TJ/2 jobs
+    const int tu = t % KS_UCH, tj = (t / KS_UCH) * (TJ / 2);
+    for (uint32_t u0 = ch0 * KS_UCH; u0 < ch1 * KS_UCH && u0 < big; u0 += KS_UCH) {
         const uint32_t u = u0 + tu;
 #pragma unroll 1
-        for (int jj = tj; jj < tj + KS_TJ / 2; ++jj) {
+        for (int jj = tj; jj < tj + TJ / 2; ++jj) {
             uint64_t a = 0;
             if (u < big) {
 #pragma unroll
@@ -267,7 +280,7 @@ k_keyswitch(const Job *__restrict__ jobs, uint32_t njobs,
                     const uint32_t klo = (uint32_t)kv, khi = (uint32_t)(kv >> 32);
                     const uint4 *dp = reinterpret_cast<const uint4 *>(&dig[ul][lev][0]);
 #pragma unroll
-                    for (int w = 0; w < KS_TJ / 4; ++w) {
+                    for (int w = 0; w < TJ / 4; ++w) {
                         const uint4 dv = dp[w];
                         lo[4 * w + 0] += (uint64_t)dv.x * klo; hi[4 * w + 0] += dv.x * khi;
                         lo[4 * w + 1] += (uint64_t)dv.y * klo; hi[4 * w + 1] += dv.y * khi;
@@ -280,10 +293,18 @@ k_keyswitch(const Job *__restrict__ jobs, uint32_t njobs,
         __syncthreads();
     }
     if (c > n) return;
+    if (S > 1) {
+#pragma unroll
+        for (int jj = 0; jj < TJ; ++jj) {
+            const uint32_t j = j0 + jj;
+            if (j < njobs) part[((size_t)z * njobs + j) * (n + 1) + c] = lo[jj] + ((uint64_t)hi[jj] << 32);
+        }
+        return;
+    }
     const uint32_t twoN_mask = (1u << log2_2N) - 1;
     const uint64_t offset = (uint64_t)hBk * colsum[c];
 #pragma unroll
-    for (int jj = 0; jj < KS_TJ; ++jj) {
+    for (int jj = 0; jj < TJ; ++jj) {
         const uint32_t j = j0 + jj;
         if (j < njobs) {
             const uint64_t sum = lo[jj] + ((uint64_t)hi[jj] << 32) - offset;   // sum_{u,lev} d * KSK
@@ -297,6 +318,29 @@ k_keyswitch(const Job *__restrict__ jobs, uint32_t njobs,
             ms[(size_t)j * (n + 1) + c] = (uint32_t)((val + (1ull << (63 - log2_2N))) >> (64 - log2_2N)) & twoN_mask;
         }
     }
+}
+
+// completes a split key switch: sum of the S partial sums, offset removal,
+// body, modulus switch (one thread per output value)
+__global__ void k_ks_finish(const Job *__restrict__ jobs, uint32_t njobs, const uint64_t *__restrict__ part,
+                            uint32_t S, const uint64_t *__restrict__ colsum, uint32_t n, uint32_t big,
+                            uint32_t ks_base_log, uint32_t log2_2N, uint32_t *__restrict__ ms)
+{
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)njobs * (n + 1)) return;
+    const uint32_t j = (uint32_t)(idx / (n + 1)), c = (uint32_t)(idx % (n + 1));
+    uint64_t sum = 0;
+    for (uint32_t z = 0; z < S; ++z) sum += part[(size_t)z * njobs * (n + 1) + idx];
+    sum -= (uint64_t)(1u << (ks_base_log - 1)) * colsum[c];
+    uint64_t val = 0 - sum;
+    if (c == n) {
+        const Job &J = jobs[j];
+        uint64_t bb = (uint64_t)(J.cst & 31) << kDeltaLog;
+        for (int s = 0; s < 3; ++s)
+            if (J.src[s]) bb += (uint64_t)(int64_t)J.coef[s] * J.src[s][big];
+        val += bb;
+    }
+    ms[idx] = (uint32_t)((val + (1ull << (63 - log2_2N))) >> (64 - log2_2N)) & ((1u << log2_2N) - 1);
 }
 
 // colsum[c] = sum over all KSK rows of column c (mod 2^64), once per context
@@ -448,15 +492,61 @@ cudaError_t launch_bsk_to_ntt_count(uint32_t N, const uint64_t *coef, uint32_t c
     return cudaGetLastError();
 }
 
-cudaError_t launch_keyswitch(const lvs_ctx *ctx, const Job *jobs, size_t njobs, uint32_t *ms, cudaStream_t s)
+KsPlan ks_plan(const lvs_ctx *ctx, size_t njobs)
+{
+    const int b = ks_bucket(njobs);
+    if (ctx->ks_tuned[b].tj) return ctx->ks_tuned[b];
+    // default: 4 jobs per CTA for tiny launches, else 16; split the input
+    // coefficients until about two CTAs per SM are busy
+    KsPlan pl;
+    pl.tj = njobs <= 4 ? 4 : 16;
+    const size_t ctas = ((njobs + pl.tj - 1) / pl.tj) * ((ctx->P.p.n + KS_THREADS) / KS_THREADS);
+    int split = 1;
+    while (split < 32 && ctas * split * 2 <= (size_t)ctx->num_sms * 2) split *= 2;
+    pl.split = split;
+    return pl;
+}
+
+size_t ks_part_words(const lvs_ctx *ctx, size_t njobs)
+{
+    const KsPlan pl = ks_plan(ctx, njobs);
+    return pl.split > 1 ? (size_t)pl.split * njobs * (ctx->P.p.n + 1) : 0;
+}
+
+cudaError_t launch_keyswitch_plan(const lvs_ctx *ctx, const Job *jobs, size_t njobs, uint32_t *ms, uint64_t *part,
+                                  KsPlan pl, cudaStream_t s)
 {
     if (njobs == 0) return cudaSuccess;
     const auto &p = ctx->P.p;
-    dim3 grid((unsigned)((njobs + KS_TJ - 1) / KS_TJ), (p.n + 1 + KS_THREADS - 1) / KS_THREADS);
+    if (!part) pl.split = 1;
+    const unsigned gy = (p.n + 1 + KS_THREADS - 1) / KS_THREADS;
     const uint32_t log2_2N = ctx->P.log_n() + 1;
-    k_keyswitch<<<grid, KS_THREADS, 0, s>>>(jobs, (uint32_t)njobs, ctx->ksk, ctx->ksk_colsum, p.n, ctx->P.big(),
-                                             p.ks_level, p.ks_base_log, log2_2N, ms);
+    if (pl.tj == 4) {
+        dim3 grid((unsigned)((njobs + 3) / 4), gy, (unsigned)pl.split);
+        k_keyswitch<4><<<grid, KS_THREADS, 0, s>>>(jobs, (uint32_t)njobs, ctx->ksk, ctx->ksk_colsum, p.n,
+                                                   ctx->P.big(), p.ks_level, p.ks_base_log, log2_2N, ms, part);
+    } else {
+        dim3 grid((unsigned)((njobs + 15) / 16), gy, (unsigned)pl.split);
+        k_keyswitch<16><<<grid, KS_THREADS, 0, s>>>(jobs, (uint32_t)njobs, ctx->ksk, ctx->ksk_colsum, p.n,
+                                                    ctx->P.big(), p.ks_level, p.ks_base_log, log2_2N, ms, part);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || pl.split == 1) return e;
+    const size_t total = njobs * (size_t)(p.n + 1);
+    k_ks_finish<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(jobs, (uint32_t)njobs, part, (uint32_t)pl.split,
+                                                                 ctx->ksk_colsum, p.n, ctx->P.big(), p.ks_base_log,
+                                                                 log2_2N, ms);
     return cudaGetLastError();
+}
+
+cudaError_t launch_keyswitch(const lvs_ctx *ctx, const Job *jobs, size_t njobs, uint32_t *ms, cudaStream_t s,
+                             int *nlaunch)
+{
+    // the context's split-K scratch (sized by ensure_scratch), if any
+    KsPlan pl = ks_plan(ctx, njobs);
+    if (!ctx->ks_part || ctx->ks_part_cap < ks_part_words(ctx, njobs)) pl.split = 1;
+    if (nlaunch) *nlaunch = njobs == 0 ? 0 : (pl.split > 1 ? 2 : 1);
+    return launch_keyswitch_plan(ctx, jobs, njobs, ms, ctx->ks_part, pl, s);
 }
 
 cudaError_t launch_blind_rotate(const lvs_ctx *ctx, const Job *jobs, size_t njobs, const uint32_t *ms,

@@ -115,6 +115,19 @@ struct Timing {
 
 }  // namespace lvs
 
+namespace lvs {
+// key-switch launch shape: jobs per CTA (4 or 16) and split of the input
+// coefficients over gridDim.z; one plan per launch-size bucket
+struct KsPlan { int tj = 0; int split = 1; };
+constexpr int kKsBuckets = 6;   // launch sizes 1-4, 5-16, 17-64, 65-256, 257-1024, more
+inline int ks_bucket(size_t njobs)
+{
+    int b = 0;
+    for (size_t lim = 4; b < kKsBuckets - 1 && njobs > lim; lim *= 4) ++b;
+    return b;
+}
+}  // namespace lvs
+
 struct lvs_ctx {
     lvs::Params P;
     int device = 0;
@@ -137,6 +150,9 @@ struct lvs_ctx {
     size_t ms_cap = 0;
     lvs::Job *jobs = nullptr;      // [jobs_cap] jobs of a whole run
     size_t jobs_cap = 0;
+    uint64_t *ks_part = nullptr;   // split key-switch partial sums
+    size_t ks_part_cap = 0;        // words
+    lvs::KsPlan ks_tuned[lvs::kKsBuckets];   // autotuned plans (tj = 0: default heuristic)
     uint64_t pbs_done = 0;
     uint64_t launches = 0;
     lvs::Timing timing;
@@ -176,7 +192,13 @@ cudaError_t upload_prime_consts(const dev::PrimeConsts &pc);
 cudaError_t prepare_kernels(uint32_t N);
 cudaError_t launch_bsk_to_ntt_count(uint32_t N, const uint64_t *coef, uint32_t count, uint32_t *out,
                                     const uint32_t *tw, const uint32_t mont[3][2], cudaStream_t s);
-cudaError_t launch_keyswitch(const lvs_ctx *ctx, const Job *jobs, size_t njobs, uint32_t *ms, cudaStream_t s);
+// nlaunch (optional): kernels launched (2 with a split: the key switch and its finishing reduction)
+cudaError_t launch_keyswitch(const lvs_ctx *ctx, const Job *jobs, size_t njobs, uint32_t *ms, cudaStream_t s,
+                             int *nlaunch = nullptr);
+cudaError_t launch_keyswitch_plan(const lvs_ctx *ctx, const Job *jobs, size_t njobs, uint32_t *ms, uint64_t *part,
+                                  KsPlan pl, cudaStream_t s);
+KsPlan ks_plan(const lvs_ctx *ctx, size_t njobs);
+size_t ks_part_words(const lvs_ctx *ctx, size_t njobs);
 cudaError_t launch_ksk_colsum(const lvs_ctx *ctx, cudaStream_t s);
 cudaError_t launch_blind_rotate(const lvs_ctx *ctx, const Job *jobs, size_t njobs, const uint32_t *ms,
                                 const uint8_t *luts, int lut_per_job, cudaStream_t s);
@@ -216,7 +238,8 @@ struct PairRows {
     const int32_t *row_of = nullptr;
     const uint8_t *plain = nullptr;
     long band = -1;          // >= 0: only cells with |i - j| <= band (square pairs)
-    size_t tap = 0;          // band: 2m rows [v[1][0], h[1][1], ..., v[m][m-1], h[m][m]]
+    size_t tap = 0;          // band: m + n rows, the readout path [v[1][0], h[1][1], ..., v[r][r-1], h[r][r],
+                             // then h[m][m+1..n] or v[r+1..m][n]], r = min(m, n)
     std::vector<uint8_t> refresh;   // empty, or [m + n + 1]: 1 if anti-diagonal i + j is refreshed
 };
 

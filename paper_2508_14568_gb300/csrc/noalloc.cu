@@ -92,7 +92,7 @@ extern "C" lvs_status lvs_pbs_batch_device_noalloc(lvs_ctx *ctx, const uint64_t 
     k_fill_raw_jobs<<<(unsigned)((count + 127) / 128), 128, 0, ctx->stream>>>(jobs, d_in, in_stride, d_out, out_stride,
                                                                             (uint32_t)count);
     LVS_CUDA(cudaGetLastError());
-    LVS_CUDA(launch_keyswitch(ctx, jobs, count, ms, ctx->stream));
+    LVS_CUDA(launch_keyswitch_plan(ctx, jobs, count, ms, nullptr, ks_plan(ctx, count), ctx->stream));
     LVS_CUDA(launch_blind_rotate(ctx, jobs, count, ms, d_lut, 1, ctx->stream));
     ctx->pbs_done += count;
     ctx->launches += 3;

@@ -47,7 +47,9 @@ struct Planner {
     bool computed(size_t i, size_t j) const
     {
         if (i < 1 || j < 1 || i > m || j > n) return false;
-        return band < 0 || (long)(i > j ? i - j : j - i) <= band;
+        if (band < 0) return true;
+        const long k = (long)j - (long)i, delta = (long)n - (long)m;
+        return std::min(0L, delta) - band <= k && k <= std::max(0L, delta) + band;
     }
     // cell (i, d - i) of slot s (0: d-2, 1: d-1, 2: d)
     const CellNoise &at(int s, size_t i, size_t d) const

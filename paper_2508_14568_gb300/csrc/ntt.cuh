@@ -59,7 +59,8 @@ __device__ __forceinline__ uint32_t mul_shoup(uint32_t w, uint32_t wsh, uint32_t
     return w * x - q * p;
 }
 
-// Montgomery reduction of T < p * 2^32: T * 2^-32 mod p in [0, 2p)
+// Montgomery reduction: T * 2^-32 mod p, below p + T / 2^32 (so in [0, 2p) for
+// T < p * 2^32); T + m p must not overflow 64 bits
 __device__ __forceinline__ uint32_t redc(uint64_t T, uint32_t p, uint32_t pinv_neg)
 {
     const uint32_t m = (uint32_t)T * pinv_neg;
@@ -87,8 +88,10 @@ struct Layout {
 };
 
 // One register pass of forward (Cooley-Tukey) stages s0 .. s0+cnt-1 on NP
-// polynomials that share positions (and hence twiddles).
-template <int LOGN, int B, int S0, int CNT, int NP, int NPA>
+// polynomials that share positions (and hence twiddles).  FRESH: the inputs of
+// the first stage are below 2p, so its lazy reduction can be skipped (outputs
+// stay below 4p).
+template <int LOGN, int B, int S0, int CNT, int NP, int NPA, bool FRESH = false>
 __device__ __forceinline__ void fwd_pass(uint32_t (&v)[NPA][16], uint32_t base, const uint2 *__restrict__ tw,
                                          uint32_t p)
 {
@@ -106,7 +109,7 @@ __device__ __forceinline__ void fwd_pass(uint32_t (&v)[NPA][16], uint32_t base, 
                 const int q0 = (g << (rb + 1)) | low, q1 = q0 | (1 << rb);
 #pragma unroll
                 for (int k = 0; k < NP; ++k) {
-                    const uint32_t x = csub(v[k][q0], p2);
+                    const uint32_t x = (FRESH && si == 0) ? v[k][q0] : csub(v[k][q0], p2);
                     const uint32_t t = mul_shoup(w.x, w.y, v[k][q1], p);
                     v[k][q0] = x + t;
                     v[k][q1] = x - t + p2;
@@ -191,15 +194,16 @@ __device__ __forceinline__ void ld2(const uint2 *buf, uint32_t (&v)[NPA][16], ui
     }
 }
 
-// Full forward transform of the 4 polynomials held in L0 layout; returns them
-// in L2 layout (bit-reversed evaluation order), values in [0, 4p).
+// Full forward transform of the 4 polynomials held in L0 layout (values in
+// [0, 2p)); returns them in L2 layout (bit-reversed evaluation order), values
+// in [0, 4p).
 // buf: N 16-byte words of this group's shared memory.  bar_id: group barrier.
 template <int LOGN>
 __device__ __forceinline__ void ntt_forward4(uint32_t (&v)[4][16], uint4 *buf, uint32_t tau,
                                              const uint2 *__restrict__ tw, uint32_t p, int bar_id)
 {
     using Lay = Layout<LOGN>;
-    fwd_pass<LOGN, Lay::B0, 0, 4, 4, 4>(v, Lay::base0(tau), tw, p);
+    fwd_pass<LOGN, Lay::B0, 0, 4, 4, 4, true>(v, Lay::base0(tau), tw, p);
     __syncwarp();
     st4<Lay::B0, 4>(buf, v, swz16(Lay::base0(tau)));
     if (Lay::T > 32) group_bar(bar_id, Lay::T); else __syncwarp();

@@ -89,28 +89,40 @@ lvs_status finish_result(lvs_ctx *ctx, lvs_result *r)
     return LVS_OK;
 }
 
-// cells (i, j) with i + j - 2 = d, 1 <= i <= m, 1 <= j <= n
+static long floor_div2(long x) { return x >= 0 ? x / 2 : -((-x + 1) / 2); }
+
+// cells (i, j) with i + j - 2 = d, 1 <= i <= m, 1 <= j <= n, inside the band:
+// diagonals k = j - i with min(0, n - m) - band <= k <= max(0, n - m) + band
+// (|i - j| <= band for m = n, Algorithm alg_levenshtein; for m != n the cells
+// where an edit path of cost <= |n - m| + 2 band can pass)
 template <class F>
 static void for_diag(const PairRows &P, long d, F f)
 {
     if (d < 0 || P.m == 0 || P.n == 0) return;
     long lo = std::max<long>(1, d + 2 - (long)P.n), hi = std::min<long>((long)P.m, d + 1);
     if (P.band >= 0) {
-        // |i - j| <= band with j = d + 2 - i  <=>  (d + 2 - band) / 2 <= i <= (d + 2 + band) / 2
-        lo = std::max(lo, (d + 2 - P.band + 1) / 2);
-        hi = std::min(hi, (d + 2 + P.band) / 2);
+        const long delta = (long)P.n - (long)P.m;
+        const long klo = std::min(0L, delta) - P.band, khi = std::max(0L, delta) + P.band;
+        // k = d + 2 - 2i in [klo, khi]  <=>  ceil((d + 2 - khi) / 2) <= i <= floor((d + 2 - klo) / 2)
+        lo = std::max(lo, -floor_div2(-(d + 2 - khi)));
+        hi = std::min(hi, floor_div2(d + 2 - klo));
     }
     for (long i = lo; i <= hi; ++i) f((size_t)i, (size_t)(d + 2 - i));
 }
 
-// band mode: cells (i, i-1) and (i, i) lie on the diagonal readout path
-// (Section 3.2: the distance is the sum of v and h along the diagonal);
-// they also copy their new v (resp. h) to the pair's tap rows.
+// band mode: the readout path from (0, 0) to (m, n) -- down the main diagonal
+// (v[i][i-1], h[i][i]) for i <= min(m, n), then along row m (h[m][j]) or down
+// column n (v[i][n]); the distance is the sum of its differences (Section 3.2).
+// A cell on the path copies its new v (tapsel 1) or h (tapsel 2) to the tap
+// row of its step.
 static Job tapped(const PairRows &P, const Arena &A, size_t i, size_t j, Job J)
 {
     if (P.band < 0) return J;
-    if (j + 1 == i) { J.tap = A.row(P.tap + 2 * (i - 1)); J.tapsel = 1; }
-    else if (j == i) { J.tap = A.row(P.tap + 2 * (i - 1) + 1); J.tapsel = 2; }
+    const size_t r = std::min(P.m, P.n);
+    if (i <= r && j + 1 == i) { J.tap = A.row(P.tap + 2 * (i - 1)); J.tapsel = 1; }
+    else if (i <= r && j == i) { J.tap = A.row(P.tap + 2 * (i - 1) + 1); J.tapsel = 2; }
+    else if (P.n > P.m && i == P.m && j > P.m) { J.tap = A.row(P.tap + 2 * r + (j - P.m - 1)); J.tapsel = 2; }
+    else if (P.m > P.n && j == P.n && i > P.n) { J.tap = A.row(P.tap + 2 * r + (i - P.n - 1)); J.tapsel = 1; }
     return J;
 }
 
@@ -236,12 +248,8 @@ lvs_status lvs_edit_distance_batch(lvs_ctx *ctx, const lvs_ct_string *const *a, 
         P.n = b[p]->len;
         P.C = a[p]->symbols;
         if (banded) {
-            // Section 3.2 / Section 6: the band and its diagonal readout are stated for m = n
-            if (P.m != P.n)
-                return set_error(LVS_ERR_ARG, "lvs_edit_distance_batch: the band needs equal lengths (pair " +
-                                                  std::to_string(p) + ")");
             P.band = o.band;
-            trows += 2 * P.m;
+            trows += P.m + P.n;
         }
         if ((st = plan_refresh(ctx, o.refresh_budget, P)) != LVS_OK) return st;
         if (a[p]->d && a[p]->ddevice == ctx->device) { P.xd = a[p]->d; P.xs = a[p]->dstride; }
@@ -262,7 +270,7 @@ lvs_status lvs_edit_distance_batch(lvs_ctx *ctx, const lvs_ct_string *const *a, 
     size_t cx = 0, cv = xrows, ch = xrows + vrows, ct = xrows + vrows + hrows, cr = ct + trows;
     for (size_t p = 0; p < npairs; ++p) {
         PairRows &P = pairs[p];
-        if (banded) { P.tap = ct; ct += 2 * P.m; }
+        if (banded) { P.tap = ct; ct += P.m + P.n; }
         if (!P.xd) { P.x = cx; cx += P.m * P.C; }
         if (!P.yd) { P.y = cx; cx += P.n * P.C; }
         P.v = cv; cv += P.m;
@@ -290,7 +298,7 @@ lvs_status lvs_edit_distance_batch(lvs_ctx *ctx, const lvs_ct_string *const *a, 
     if (st != LVS_OK) { arena_free(ctx, A); return st; }
     size_t first = 0;
     for (size_t p = 0; p < npairs; ++p) {
-        const size_t cnt = banded ? 2 * pairs[p].m : pairs[p].n;
+        const size_t cnt = banded ? pairs[p].m + pairs[p].n : pairs[p].n;
         r->items.push_back({pairs[p].m, pairs[p].n, first, cnt, banded ? 0L : (long)pairs[p].m});
         first += cnt;
     }

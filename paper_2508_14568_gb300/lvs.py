@@ -35,6 +35,7 @@ EXPORTS = [
     "lvs_poly_mul_device", "lvs_ctx_set_timing", "lvs_ctx_kernel_stats", "lvs_ctx_pbs_count",
     "lvs_ctx_launch_count", "lvs_ct_string_upload", "lvs_pbs_batch_device_noalloc",
     "lvs_ctx_prepare_fft64", "lvs_pbs_batch_device_fft64", "lvs_noise_budget", "lvs_noise_plan",
+    "lvs_ctx_autotune", "lvs_ctx_ks_plan", "lvs_ctx_set_ks_plan", "lvs_probe_int_mul",
     "lvs_server_create", "lvs_server_submit", "lvs_server_poll", "lvs_server_stats_get", "lvs_server_free",
 ]
 
@@ -132,6 +133,10 @@ def _declare(L):
         "lvs_pbs_batch_device": ([vp, vp, sz, vp, vp, sz, sz], i32),
         "lvs_pbs_batch_device_fft64": ([vp, vp, sz, vp, vp, sz, sz], i32),
         "lvs_ctx_prepare_fft64": ([vp, vp], i32),
+        "lvs_ctx_autotune": ([vp], i32),
+        "lvs_probe_int_mul": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
+        "lvs_ctx_ks_plan": ([vp, sz, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
+        "lvs_ctx_set_ks_plan": ([vp, sz, i32, i32], i32),
         "lvs_noise_budget": ([ctypes.POINTER(lvs_params), ctypes.c_double, ctypes.POINTER(ctypes.c_double)], i32),
         "lvs_noise_plan": ([sz, sz, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_uint8),
                             ctypes.POINTER(ctypes.c_double)], i32),
@@ -301,6 +306,11 @@ def lvs_ctx_create(sk, device=0, stream=None):
     c = ctypes.c_void_p()
     _check(lib().lvs_ctx_create(sk, device, ctypes.c_void_p(stream) if stream else None, ctypes.byref(c)))
     return Context(c.value, owner=sk)
+
+
+def lvs_ctx_free(ctx):
+    """Frees the context now (otherwise when the handle is collected)."""
+    ctx.__del__()
 
 
 def lvs_ctx_synchronize(ctx):
@@ -486,6 +496,28 @@ def lvs_server_stats_get(server):
 
 def lvs_pbs_batch_device(ctx, d_in, in_stride, d_lut, d_out, out_stride, count):
     _check(lib().lvs_pbs_batch_device(ctx, _ptr(d_in), in_stride, _ptr(d_lut), _ptr(d_out), out_stride, count))
+
+
+def lvs_probe_int_mul(device=0):
+    """(low-half, high-half) 32-bit multiplies per SM per clock, measured."""
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(lib().lvs_probe_int_mul(device, ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+def lvs_ctx_autotune(ctx):
+    _check(lib().lvs_ctx_autotune(ctx))
+
+
+def lvs_ctx_ks_plan(ctx, njobs):
+    """(jobs per CTA, split) of the key switch for a launch of njobs PBS."""
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().lvs_ctx_ks_plan(ctx, njobs, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def lvs_ctx_set_ks_plan(ctx, njobs, jobs_per_cta, split):
+    _check(lib().lvs_ctx_set_ks_plan(ctx, njobs, jobs_per_cta, split))
 
 
 def lvs_ctx_prepare_fft64(ctx, sk):

@@ -1,8 +1,9 @@
 """Banded Leuvenshtein (Algorithm alg_levenshtein's |i - j| <= band, Section
-3.2: "Exact Skip" with band = floor(m/2), approximate with smaller bands) on the
-GPU: the diagonal readout path is bit-exact with the oracle's banded run, the
-distance equals Wagner-Fischer for the exact-skip band and the plaintext
-banded oracle otherwise, and fewer PBS run."""
+3.2: "Exact Skip" with band = floor(m/2), approximate with smaller bands; for
+m != n the band widened to the diagonals between 0 and n - m) on the GPU: the
+readout path is bit-exact with the oracle's banded run, the distance equals
+Wagner-Fischer for the exact bands and the plaintext banded oracle otherwise,
+and fewer PBS run."""
 import numpy as np
 import pytest
 
@@ -87,8 +88,39 @@ def test_band_path_bit_exact_vs_oracle(small):
             assert d[0] == T.decrypt_path(K, res["diag"])
 
 
-def test_band_needs_square_pairs(small):
+def test_non_square_band_bit_exact_and_exact(small):
+    """m != n: the band widened to the diagonals between 0 and n - m
+    (plain.in_band) with the path readout; exact from band ceil(min/2) on,
+    bit-exact with the oracle's banded run, and PBS only inside the band."""
+    ck, ctx, K = small
+    cases = [("kitten", "sitting!!", P.ALPHA_ASCII7), ("GATTACAGA", "GCAT", P.ALPHA_DNA4),
+             ("ab", "abcdefg", P.ALPHA_ASCII7), ("TTTTTTT", "T", P.ALPHA_DNA4)]
+    for k, (a, b, alpha) in enumerate(cases):
+        m, n = len(a), len(b)
+        for band in sorted({0, 1, (min(m, n) + 1) // 2}):
+            r, d, npbs = _run(ck, ctx, [(a, b)], alpha, band, 15 + k)
+            xa = T.encrypt_string(K, a, alpha, 15 + k, 0)
+            yb = T.encrypt_string(K, b, alpha, 15 + k, 1)
+            res = T.lvs_encrypted(K, xa, yb, alpha, parallel=True, band=band)
+            assert np.array_equal(L.lvs_result_export(r, 0, K.big_dim), np.stack(res["path"]))
+            E9 = [[9 if i and j and a[i - 1] == b[j - 1] else 0 for j in range(n + 1)] for i in range(m + 1)]
+            h, v = P.lvs_on_eq9(E9, m, n, band=band)
+            assert d[0] == P.readout_path(h, v, m, n) == T.decrypt_path(K, res["path"])
+            assert d[0] >= P.wf_distance(a, b)
+            if band >= (min(m, n) + 1) // 2:
+                assert d[0] == P.wf_distance(a, b)
+            assert npbs == (P.eq_pbs_per_cell(alpha) + 1) * P.band_cells_general(m, n, band)
+
+
+def test_non_square_band_batch_mixed_lengths(small):
     ck, ctx, _ = small
-    with pytest.raises(L.LvsError) as e:
-        _run(ck, ctx, [("abc", "ab")], P.ALPHA_ASCII7, 1, 14)
-    assert e.value.status == L.LVS_ERR_ARG
+    import random
+    rng = random.Random(21)
+    pairs = []
+    for _ in range(30):
+        m, n = rng.randint(1, 11), rng.randint(1, 11)
+        pairs.append(("".join(rng.choice("abcd") for _ in range(m)), "".join(rng.choice("abcd") for _ in range(n))))
+    band = 6    # >= ceil(min(m, n) / 2) for every pair: exact
+    r, d, npbs = _run(ck, ctx, pairs, P.ALPHA_ASCII7, band, 22)
+    assert d == [P.wf_distance(a, b) for a, b in pairs]
+    assert npbs == sum(3 * P.band_cells_general(len(a), len(b), band) for a, b in pairs)

@@ -1,0 +1,81 @@
+"""Key-switch launch plans (jobs per CTA, split of the input coefficients
+over CTAs) and their autotuner: every plan is bit-exact with the oracle's key
+switch + modulus switch (Section 2.2), and autotuning changes no result."""
+import numpy as np
+import pytest
+
+from oracle import plain as P
+from oracle import tfhe as T
+from paper_2508_14568_gb300 import lvs as L
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def full():
+    ck, sk = L.lvs_keygen(L.lvs_params_default(), 0)
+    return ck, L.lvs_ctx_create(sk, 0), T.Keys(T.params_lvs(), 0)
+
+
+PLANS = [(4, 1), (4, 8), (16, 1), (16, 2), (16, 32), (16, 3)]
+
+
+@pytest.mark.parametrize("count", [1, 3, 17, 70])
+def test_every_plan_bit_exact(full, count):
+    ck, ctx, K = full
+    p = K.params
+    big = K.big_dim
+    cts = np.stack([T.encrypt(K, (5 * i) % 32, 12, 3, i) for i in range(count)])
+    want = np.stack([T.modswitch(K, T.keyswitch(K, c)) for c in cts])
+    d_in = torch.from_numpy(cts.view(np.int64)).cuda()
+    for tj, split in PLANS:
+        L.lvs_ctx_set_ks_plan(ctx, count, tj, split)
+        assert L.lvs_ctx_ks_plan(ctx, count) == (tj, split)
+        d_out = torch.zeros((count, p.n + 1), dtype=torch.int32, device="cuda")
+        L.lvs_keyswitch_batch_device(ctx, d_in, big + 1, d_out, count)
+        L.lvs_ctx_synchronize(ctx)
+        got = d_out.cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, want), (tj, split)
+    L.lvs_ctx_set_ks_plan(ctx, count, 0, 1)   # back to the default
+
+
+def test_set_plan_rejects_bad_shapes(full):
+    _, ctx, _ = full
+    for tj, split in [(8, 1), (16, 0), (16, 33), (-4, 1)]:
+        with pytest.raises(L.LvsError):
+            L.lvs_ctx_set_ks_plan(ctx, 10, tj, split)
+
+
+def test_autotune_keeps_results(full):
+    ck, ctx, K = full
+    big = K.big_dim
+    msgs = [0, 9, 17, 31, 4, 12]
+    luts = np.asarray([P.LUT_MIN, P.LUT_EQ9, P.LUT_EQ, P.LUT_MIN, P.LUT_V, P.LUT_EQ], np.uint8)
+    cts = np.stack([T.encrypt(K, m, 8, 1, i) for i, m in enumerate(msgs)])
+    d_in = torch.from_numpy(cts.view(np.int64)).cuda()
+    d_lut = torch.from_numpy(luts).cuda()
+
+    def run():
+        d_out = torch.zeros_like(d_in)
+        L.lvs_pbs_batch_device(ctx, d_in, big + 1, d_lut, d_out, big + 1, len(msgs))
+        L.lvs_ctx_synchronize(ctx)
+        return d_out.cpu().numpy().view(np.uint64).copy()
+
+    before = run()
+    L.lvs_ctx_autotune(ctx)
+    plans = [L.lvs_ctx_ks_plan(ctx, n) for n in (1, 10, 50, 200, 800, 5000)]
+    assert all(tj in (4, 16) and 1 <= s <= 32 for tj, s in plans)
+    after = run()
+    assert np.array_equal(before, after)
+    assert np.array_equal(after, T.pbs_many(K, cts, luts.astype(np.uint32)))
+
+
+def test_int_mul_probe_plausible():
+    """The measured multiply issue rates that set the blind rotation's
+    roofline: positive, at most 128 per SM per clock (4 sub-partitions x 32
+    lanes), and the high half no faster than the low half."""
+    lo, hi = L.lvs_probe_int_mul(0)
+    assert 8 <= lo <= 128 and 4 <= hi <= 128
+    assert hi <= lo * 1.05

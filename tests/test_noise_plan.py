@@ -11,7 +11,7 @@ from paper_2508_14568_gb300 import lvs as L
 
 CASES = [(20, 20, -1, 25), (20, 20, -1, 60), (15, 22, -1, 40), (22, 15, -1, 33), (16, 16, 5, 30),
          (16, 16, 2, 11), (12, 12, -1, 11), (30, 30, -1, 0), (9, 9, 3, 0), (1, 1, -1, 5), (1, 17, -1, 12),
-         (17, 1, -1, 12), (25, 25, 8, 100)]
+         (17, 1, -1, 12), (25, 25, 8, 100), (12, 20, 3, 30), (20, 9, 2, 25), (7, 15, 0, 0)]
 
 
 @pytest.mark.parametrize("m,n,band,budget", CASES)
