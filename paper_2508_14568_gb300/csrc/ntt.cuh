@@ -87,6 +87,17 @@ struct Layout {
     __device__ static __forceinline__ uint32_t base2(uint32_t tau) { return tau << 4; }
 };
 
+// Position of register q (= qg << B) of the thread with base `base`, as far as
+// the twiddle index of stages s <= 3 needs it: in the L0 layout (B = LOGN - 4)
+// the thread bits lie below bit LOGN - 4 and are shifted out by
+// e >> (LOGN - s), so the index is the same for every thread (a compile-time
+// constant, one broadcast load).
+template <int LOGN, int B>
+__device__ __forceinline__ uint32_t tw_pos(uint32_t base, int qg)
+{
+    return (B == LOGN - 4) ? ((uint32_t)qg << B) : (base | ((uint32_t)qg << B));
+}
+
 // One register pass of forward (Cooley-Tukey) stages s0 .. s0+cnt-1 on NP
 // polynomials that share positions (and hence twiddles).  FRESH: the inputs of
 // the first stage are below 2p, so its lazy reduction can be skipped (outputs
@@ -102,8 +113,7 @@ __device__ __forceinline__ void fwd_pass(uint32_t (&v)[NPA][16], uint32_t base, 
         const int rb = LOGN - s - 1 - B;
 #pragma unroll
         for (int g = 0; g < (1 << (3 - rb)); ++g) {
-            const uint32_t eg = base | ((uint32_t)(g << (rb + 1)) << B);
-            const uint2 w = __ldg(tw + (1u << s) + (eg >> (LOGN - s)));
+            const uint2 w = __ldg(tw + (1u << s) + (tw_pos<LOGN, B>(base, g << (rb + 1)) >> (LOGN - s)));
 #pragma unroll
             for (int low = 0; low < (1 << rb); ++low) {
                 const int q0 = (g << (rb + 1)) | low, q1 = q0 | (1 << rb);
@@ -131,8 +141,7 @@ __device__ __forceinline__ void inv_pass(uint32_t (&v)[NPA][16], uint32_t base, 
         const int rb = LOGN - s - 1 - B;
 #pragma unroll
         for (int g = 0; g < (1 << (3 - rb)); ++g) {
-            const uint32_t eg = base | ((uint32_t)(g << (rb + 1)) << B);
-            const uint2 w = __ldg(tw + (1u << s) + (eg >> (LOGN - s)));
+            const uint2 w = __ldg(tw + (1u << s) + (tw_pos<LOGN, B>(base, g << (rb + 1)) >> (LOGN - s)));
 #pragma unroll
             for (int low = 0; low < (1 << rb); ++low) {
                 const int q0 = (g << (rb + 1)) | low, q1 = q0 | (1 << rb);

@@ -4,8 +4,9 @@
 // one high-half 32-bit multiplies).
 //
 // One CTA of 1024 threads per SM (its unused dynamic shared memory keeps a
-// second CTA off the SM) runs sixteen independent multiply chains per thread
-// (enough multiplies in flight to cover the high-half latency);
+// second CTA off the SM) runs 16 or 32 independent multiply chains per thread
+// (the faster of the two is kept, so that latency does not hide the issue
+// rate);
 // thread 0 reads the SM clock counter around the loop (after a barrier on both
 // sides), so the rate is in multiplies per SM clock and does not depend on the
 // clock frequency the GPU runs at.
@@ -18,10 +19,9 @@ namespace lvs {
 
 constexpr int kProbeThreads = 1024;
 constexpr int kProbeIters = 2048;
-constexpr int kChains = 16;
 constexpr int kProbeSmem = 160 << 10;   // more than half an SM's shared memory
 
-template <int MODE>
+template <int MODE, int kChains>
 __global__ void __launch_bounds__(kProbeThreads) k_probe_mul(uint32_t *out, long long *cycles, uint32_t seed)
 {
     uint32_t a[kChains];
@@ -71,21 +71,23 @@ extern "C" lvs_status lvs_probe_int_mul(int device, double *lo_per_sm_clk, doubl
         return set_error(LVS_ERR_OOM, "lvs_probe_int_mul: device allocation failed");
     }
     double rate[2] = {0, 0};
-    cudaError_t e = cudaFuncSetAttribute(k_probe_mul<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_probe_mul<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem);
+    cudaError_t e = cudaSuccess;
     std::vector<long long> h(sms);
-    for (int mode = 0; mode < 2 && e == cudaSuccess; ++mode) {
-        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // first run warms up
-            if (mode == 0) k_probe_mul<0><<<sms, kProbeThreads, kProbeSmem>>>(out, cyc, 3u + rep);
-            else k_probe_mul<1><<<sms, kProbeThreads, kProbeSmem>>>(out, cyc, 3u + rep);
+    // (mode, chains) variants; each runs twice, the first run warms up
+    void (*kern[4])(uint32_t *, long long *, uint32_t) = {k_probe_mul<0, 16>, k_probe_mul<0, 32>,
+                                                          k_probe_mul<1, 16>, k_probe_mul<1, 32>};
+    const int chains[4] = {16, 32, 16, 32};
+    for (int v = 0; v < 4 && e == cudaSuccess; ++v) {
+        e = cudaFuncSetAttribute(kern[v], cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem);
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            kern[v]<<<sms, kProbeThreads, kProbeSmem>>>(out, cyc, 3u + rep);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, sms * sizeof(long long), cudaMemcpyDeviceToHost);
         }
         if (e == cudaSuccess) {
             std::sort(h.begin(), h.end());
-            const double ops = (double)kProbeThreads * kProbeIters * kChains;
-            rate[mode] = ops / (double)h[sms / 2];
+            const double ops = (double)kProbeThreads * kProbeIters * chains[v];
+            rate[v / 2] = std::max(rate[v / 2], ops / (double)h[sms / 2]);
         }
     }
     cudaFree(out);
