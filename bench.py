@@ -295,6 +295,9 @@ def run_lvs(args):
     stream = torch.cuda.Stream(device=local)
     torch.cuda.set_stream(stream)
     ctx = L.lvs_ctx_create(sk, local, stream)
+    # key-switch launch shapes by measurement (before any timing)
+    L.lvs_ctx_autotune(ctx)
+    ks_plans = {str(nj): list(L.lvs_ctx_ks_plan(ctx, nj)) for nj in (4, 16, 64, 256, 1024, 4096)}
     big = params.k * params.N
     cells = sum(len(a) * len(b) for a, b in pairs)
     want = [P.wf_distance(a, b) for a, b in pairs]
@@ -470,7 +473,9 @@ def run_lvs(args):
                                           n_sms, modmul_per_sm_clk, sm_mhz_max, mul_lo, mul_hi),
                          "frac_all_mul_at_lo_rate": (3 * w_mod * units_per_launch / avg_launch_s / 1e12 / peak_mul32)
                          if achieved else None},
-            "kernels": {"blind_rotate": br, "keyswitch": ks},
+            "kernels": {"blind_rotate": br, "keyswitch": ks,
+                        "ks_plans": {"note": "launch size bucket end -> [PBS per CTA, split] (lvs_ctx_autotune)",
+                                     "plans": ks_plans}},
             "latency_ms": {"p50": batched_latency_ms, "p99": batched_latency_ms,
                            "note": "batched: all pairs of a step complete together"},
             "one_pair_at_a_time": serial,
