@@ -230,6 +230,13 @@ lvs_status lvs_edit_distance_batch(lvs_ctx *ctx, const lvs_ct_string *const *a,
  * 128 / 27 / 4 symbols).  Cost: nsub * len * (2 or 1) PBS.  Device memory. */
 lvs_status lvs_preprocess(lvs_ctx *ctx, const lvs_ct_string *enc, const uint8_t *subset,
                           size_t nsub, lvs_eq_table **out);
+/* The tables of count encrypted strings at once (same subset for all): every
+ * lookup of every string in the same launches (2 launch steps; 1 for DNA), the
+ * offline phase of Section 5 at scale (an encrypted database of strings to be
+ * queried with plaintext strings).  outs[k] receives the table of encs[k];
+ * on error nothing is returned. */
+lvs_status lvs_preprocess_batch(lvs_ctx *ctx, const lvs_ct_string *const *encs, size_t count,
+                                const uint8_t *subset, size_t nsub, lvs_eq_table **outs);
 void lvs_eq_table_free(lvs_eq_table *t);
 
 /* Online phase of Section 5: distance of each preprocessed encrypted string

@@ -44,20 +44,12 @@ class _Tracker:
         return sum(a * a for a in x.values())
 
 
-def key_variances(m, n, band=None, refresh=frozenset()):
-    """Variances (eps^2_PBS units) of the key of every computed cell (i, j)
-    and of its swapped key (1 - dh_in) + 3 (1 + dv_in) + EQ9, which a
-    refreshed cell bootstraps for dh_out.
-
-    Boundary values (v[i][0], h[0][j]) and cells outside the band keep the
-    plaintext OneMatrix value 1 and carry no noise.  A cell on a refreshed
-    anti-diagonal d = i + j outputs fresh dv, dh.  Returns
-    {(i, j): (var_key, var_swapped_key)}."""
+def _track(m, n, band, refresh):
     T = _Tracker()
     zero = {}
     v = {}   # (i, j) -> noise of v[i][j]
     h = {}
-    out = {}
+    keys = {}
     for d in range(2, m + n + 1):
         for i in range(max(1, d - n), min(m, d - 1) + 1):
             j = d - i
@@ -68,7 +60,7 @@ def key_variances(m, n, band=None, refresh=frozenset()):
             eq9 = T.unit()
             key = T.lin((-1, dv_in), (3, dh_in), (1, eq9))
             key_sw = T.lin((3, dv_in), (-1, dh_in), (1, eq9))
-            out[(i, j)] = (T.var(key), T.var(key_sw))
+            keys[(i, j)] = (T.var(key), T.var(key_sw))
             if d in refresh:
                 v[(i, j)] = T.unit()
                 h[(i, j)] = T.unit()
@@ -76,7 +68,26 @@ def key_variances(m, n, band=None, refresh=frozenset()):
                 M = T.unit()
                 v[(i, j)] = T.lin((1, M), (-1, dh_in))
                 h[(i, j)] = T.lin((1, M), (-1, dv_in))
-    return out
+    return keys, v, h
+
+
+def key_variances(m, n, band=None, refresh=frozenset()):
+    """Variances (eps^2_PBS units) of the key of every computed cell (i, j)
+    and of its swapped key (1 - dh_in) + 3 (1 + dv_in) + EQ9, which a
+    refreshed cell bootstraps for dh_out.
+
+    Boundary values (v[i][0], h[0][j]) and cells outside the band keep the
+    plaintext OneMatrix value 1 and carry no noise.  A cell on a refreshed
+    anti-diagonal d = i + j outputs fresh dv, dh.  Returns
+    {(i, j): (var_key, var_swapped_key)}."""
+    return _track(m, n, band, refresh)[0]
+
+
+def output_variances(m, n, band=None, refresh=frozenset()):
+    """Variances (eps^2_PBS units) of the outputs v[i][j], h[i][j] of every
+    computed cell: {(i, j): (var_v, var_h)}."""
+    _, v, h = _track(m, n, band, refresh)
+    return {c: (_Tracker.var(v[c]), _Tracker.var(h[c])) for c in v}
 
 
 def key_variance_closed_form(i, j):

@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <cstring>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lvs_internal.hpp"
 #include "ntt.cuh"
 
@@ -119,6 +121,7 @@ static void reap_graphs(lvs_ctx *ctx, bool wait)
 
 static lvs_status launch_step(lvs_ctx *ctx, const Job *d_jobs, size_t nj, bool timed)
 {
+    nvtxMarkA(("lvs step: " + std::to_string(nj) + " PBS").c_str());
     cudaEvent_t a = nullptr, b = nullptr, c = nullptr;
     if (timed) {
         a = pool_event(ctx); b = pool_event(ctx); c = pool_event(ctx);
@@ -137,11 +140,22 @@ static lvs_status launch_step(lvs_ctx *ctx, const Job *d_jobs, size_t nj, bool t
     return LVS_OK;
 }
 
+// A step wider than this runs as several launches (its jobs are independent):
+// bounded launch time and modulus-switch scratch.
+constexpr size_t kMaxLaunchJobs = 1u << 16;
+
 lvs_status run_steps(lvs_ctx *ctx, const std::vector<Job> &jobs, const std::vector<size_t> &off, bool use_graph)
 {
     size_t widest = 0;
     for (size_t s = 0; s + 1 < off.size(); ++s) widest = std::max(widest, off[s + 1] - off[s]);
+    widest = std::min(widest, kMaxLaunchJobs);
     if (jobs.empty()) return LVS_OK;
+    // NVTX range around the whole run (visible to nsys / ncu when attached; a
+    // no-op otherwise)
+    struct Range {
+        Range(size_t steps) { nvtxRangePushA(("lvs wavefront: " + std::to_string(steps) + " steps").c_str()); }
+        ~Range() { nvtxRangePop(); }
+    } range(off.size() - 1);
     reap_graphs(ctx, false);
     lvs_status st = ensure_scratch(ctx, jobs.size(), widest);
     if (st != LVS_OK) return st;
@@ -154,7 +168,8 @@ lvs_status run_steps(lvs_ctx *ctx, const std::vector<Job> &jobs, const std::vect
         LVS_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
         lvs_status lst = LVS_OK;
         for (size_t s = 0; s + 1 < off.size() && lst == LVS_OK; ++s)
-            if (off[s + 1] > off[s]) lst = launch_step(ctx, ctx->jobs + off[s], off[s + 1] - off[s], false);
+            for (size_t c0 = off[s]; c0 < off[s + 1] && lst == LVS_OK; c0 += kMaxLaunchJobs)
+                lst = launch_step(ctx, ctx->jobs + c0, std::min(kMaxLaunchJobs, off[s + 1] - c0), false);
         cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
         if (lst != LVS_OK) { if (graph) cudaGraphDestroy(graph); return lst; }
         if (ce != cudaSuccess) return cuda_error(ce, "cudaStreamEndCapture");
@@ -169,11 +184,11 @@ lvs_status run_steps(lvs_ctx *ctx, const std::vector<Job> &jobs, const std::vect
         LVS_CUDA(cudaEventRecord(done, ctx->stream));
         ctx->graphs.push_back({exec, done});
     } else {
-        for (size_t s = 0; s + 1 < off.size(); ++s) {
-            if (off[s + 1] == off[s]) continue;
-            st = launch_step(ctx, ctx->jobs + off[s], off[s + 1] - off[s], timed);
-            if (st != LVS_OK) return st;
-        }
+        for (size_t s = 0; s + 1 < off.size(); ++s)
+            for (size_t c0 = off[s]; c0 < off[s + 1]; c0 += kMaxLaunchJobs) {
+                st = launch_step(ctx, ctx->jobs + c0, std::min(kMaxLaunchJobs, off[s + 1] - c0), timed);
+                if (st != LVS_OK) return st;
+            }
     }
     ctx->pbs_done += jobs.size();
     return LVS_OK;

@@ -361,79 +361,107 @@ lvs_status lvs_eq(lvs_ctx *ctx, const lvs_ct_string *a, size_t i, const lvs_ct_s
     return LVS_OK;
 }
 
-lvs_status lvs_preprocess(lvs_ctx *ctx, const lvs_ct_string *enc, const uint8_t *subset, size_t nsub,
-                          lvs_eq_table **out)
+lvs_status lvs_preprocess_batch(lvs_ctx *ctx, const lvs_ct_string *const *encs, size_t count, const uint8_t *subset,
+                                size_t nsub, lvs_eq_table **outs)
 {
-    if (!ctx || !out) return set_error(LVS_ERR_ARG, "lvs_preprocess: NULL argument");
-    lvs_status st = check_ctx_string(ctx, enc);
-    if (st != LVS_OK) return st;
-    std::vector<uint8_t> sub;
-    if (subset) sub.assign(subset, subset + nsub);
-    else
-        for (uint32_t s = 0; s < alphabet_size(enc->alphabet); ++s) sub.push_back(alphabet_char(enc->alphabet, s));
-    lvs_eq_table *t = new (std::nothrow) lvs_eq_table;
-    if (!t) return set_error(LVS_ERR_OOM, "lvs_preprocess: host allocation failed");
-    t->P = ctx->P;
-    t->device = ctx->device;
-    t->alphabet = enc->alphabet;
-    t->len = enc->len;
-    t->stride = (size_t)ctx->P.big() + 2;
-    for (int c = 0; c < 256; ++c) t->row_of[c] = -1;
-    std::vector<std::pair<uint32_t, uint32_t>> sym(sub.size());
-    for (size_t r = 0; r < sub.size(); ++r) {
-        uint32_t v[2] = {0, 0};
-        if (!encode_char(enc->alphabet, sub[r], v) || t->row_of[sub[r]] >= 0) {
-            delete t;
-            return set_error(LVS_ERR_ARG, "lvs_preprocess: subset character " + std::to_string(sub[r]) +
-                                              " is outside the alphabet or repeated");
+    if (!ctx || !outs || (count && !encs)) return set_error(LVS_ERR_ARG, "lvs_preprocess: NULL argument");
+    lvs_status st = LVS_OK;
+    for (size_t k = 0; k < count; ++k)
+        if ((st = check_ctx_string(ctx, encs[k])) != LVS_OK) return st;
+    std::vector<lvs_eq_table *> tabs(count, nullptr);
+    std::vector<std::vector<std::pair<uint32_t, uint32_t>>> syms(count);
+    auto free_all = [&]() {
+        for (auto t : tabs) lvs_eq_table_free(t);
+    };
+    // host side of every table: subset rows and their symbol values
+    for (size_t k = 0; k < count; ++k) {
+        const lvs_ct_string *enc = encs[k];
+        std::vector<uint8_t> sub;
+        if (subset) sub.assign(subset, subset + nsub);
+        else
+            for (uint32_t s2 = 0; s2 < alphabet_size(enc->alphabet); ++s2) sub.push_back(alphabet_char(enc->alphabet, s2));
+        lvs_eq_table *t = new (std::nothrow) lvs_eq_table;
+        if (!t) { free_all(); return set_error(LVS_ERR_OOM, "lvs_preprocess: host allocation failed"); }
+        tabs[k] = t;
+        t->P = ctx->P;
+        t->device = ctx->device;
+        t->alphabet = enc->alphabet;
+        t->len = enc->len;
+        t->stride = (size_t)ctx->P.big() + 2;
+        for (int c = 0; c < 256; ++c) t->row_of[c] = -1;
+        syms[k].resize(sub.size());
+        for (size_t r = 0; r < sub.size(); ++r) {
+            uint32_t v[2] = {0, 0};
+            if (!encode_char(enc->alphabet, sub[r], v) || t->row_of[sub[r]] >= 0) {
+                free_all();
+                return set_error(LVS_ERR_ARG, "lvs_preprocess: subset character " + std::to_string(sub[r]) +
+                                                  " is outside the alphabet or repeated");
+            }
+            t->row_of[sub[r]] = (int32_t)r;
+            syms[k][r] = {v[0], v[1]};
         }
-        t->row_of[sub[r]] = (int32_t)r;
-        sym[r] = {v[0], v[1]};
+        t->subset = sub;
     }
-    t->subset = sub;
-    const size_t m = enc->len, C = enc->symbols, R = sub.size();
     LVS_CUDA(cudaSetDevice(ctx->device));
     std::lock_guard<std::mutex> lock(ctx->mu);
-    if (R * m && cudaMalloc((void **)&t->d, R * m * t->stride * 8) != cudaSuccess) {
-        cudaGetLastError();
-        delete t;
-        return set_error(LVS_ERR_OOM, "lvs_preprocess: device allocation of the table failed");
+    // arena: per string x (m*C) and, for two lookups, EQ1 (R*m)
+    size_t rows = 0;
+    std::vector<size_t> base(count);
+    for (size_t k = 0; k < count; ++k) {
+        const size_t m = encs[k]->len, C = encs[k]->symbols, R = tabs[k]->subset.size();
+        base[k] = rows;
+        rows += m * C + (C == 2 ? R * m : 0);
+        if (R * m && cudaMalloc((void **)&tabs[k]->d, R * m * tabs[k]->stride * 8) != cudaSuccess) {
+            cudaGetLastError();
+            free_all();
+            return set_error(LVS_ERR_OOM, "lvs_preprocess: device allocation of the table failed");
+        }
     }
-    Arena A;   // rows: x (m*C), eq1 (R*m)
-    if ((st = arena_alloc(ctx, m * C + (C == 2 ? R * m : 0), A)) != LVS_OK) { lvs_eq_table_free(t); return st; }
-    if ((st = upload_string(ctx, enc, A, 0)) != LVS_OK) { arena_free(ctx, A); lvs_eq_table_free(t); return st; }
+    Arena A;
+    if ((st = arena_alloc(ctx, rows, A)) != LVS_OK) { free_all(); return st; }
+    for (size_t k = 0; k < count && st == LVS_OK; ++k) st = upload_string(ctx, encs[k], A, base[k]);
+    if (st != LVS_OK) { arena_free(ctx, A); free_all(); return st; }
+    // step 0: EQ1 = PBS(x1_i - sigma1; LUT_EQ) (DNA: EQ9 = PBS(x_i - sigma; LUT_EQ9));
+    // step 1: EQ9 = PBS(2 (x2_i - sigma2) + 1 - EQ1; LUT_EQ9) -- all strings in the same launches
     std::vector<Job> jobs;
     std::vector<size_t> off{0};
-    auto T = [&](size_t r, size_t i) { return t->d + (r * m + i) * t->stride; };
-    if (C == 2) {
-        // EQ1 = PBS(x1_i - sigma1; LUT_EQ), EQ9 = PBS(2 (x2_i - sigma2) + 1 - EQ1; LUT_EQ9)
-        for (size_t r = 0; r < R; ++r)
-            for (size_t i = 0; i < m; ++i)
-                jobs.push_back(make_job(A.row(i * C), 1, nullptr, 0, nullptr, 0, -(int)sym[r].first, LUT_EQ, JOB_STORE,
-                                        A.row(m * C + r * m + i), nullptr));
-        off.push_back(jobs.size());
-        for (size_t r = 0; r < R; ++r)
-            for (size_t i = 0; i < m; ++i)
-                jobs.push_back(make_job(A.row(i * C + 1), 2, A.row(m * C + r * m + i), -1, nullptr, 0,
-                                        1 - 2 * (int)sym[r].second, LUT_EQ9, JOB_STORE, T(r, i), nullptr));
-        off.push_back(jobs.size());
-    } else {
-        for (size_t r = 0; r < R; ++r)
-            for (size_t i = 0; i < m; ++i)
-                jobs.push_back(make_job(A.row(i), 1, nullptr, 0, nullptr, 0, -(int)sym[r].first, LUT_EQ9, JOB_STORE,
-                                        T(r, i), nullptr));
+    for (int step = 0; step < 2; ++step) {
+        for (size_t k = 0; k < count; ++k) {
+            lvs_eq_table *t = tabs[k];
+            const size_t m = encs[k]->len, C = encs[k]->symbols, R = t->subset.size(), b0 = base[k];
+            auto T = [&](size_t r, size_t i) { return t->d + (r * m + i) * t->stride; };
+            for (size_t r = 0; r < R; ++r)
+                for (size_t i = 0; i < m; ++i) {
+                    if (C == 2 && step == 0)
+                        jobs.push_back(make_job(A.row(b0 + i * C), 1, nullptr, 0, nullptr, 0, -(int)syms[k][r].first,
+                                                LUT_EQ, JOB_STORE, A.row(b0 + m * C + r * m + i), nullptr));
+                    else if (C == 2)
+                        jobs.push_back(make_job(A.row(b0 + i * C + 1), 2, A.row(b0 + m * C + r * m + i), -1, nullptr,
+                                                0, 1 - 2 * (int)syms[k][r].second, LUT_EQ9, JOB_STORE, T(r, i),
+                                                nullptr));
+                    else if (step == 0)
+                        jobs.push_back(make_job(A.row(b0 + i), 1, nullptr, 0, nullptr, 0, -(int)syms[k][r].first,
+                                                LUT_EQ9, JOB_STORE, T(r, i), nullptr));
+                }
+        }
         off.push_back(jobs.size());
     }
     st = run_steps(ctx, jobs, off, false);
     arena_free(ctx, A);
-    if (st == LVS_OK) {
-        if (cudaEventCreateWithFlags(&t->done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventRecord(t->done, ctx->stream) != cudaSuccess)
+    for (size_t k = 0; k < count && st == LVS_OK; ++k)
+        if (cudaEventCreateWithFlags(&tabs[k]->done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(tabs[k]->done, ctx->stream) != cudaSuccess)
             st = set_error(LVS_ERR_CUDA, "lvs_preprocess: event");
-    }
-    if (st != LVS_OK) { lvs_eq_table_free(t); return st; }
-    *out = t;
+    if (st != LVS_OK) { free_all(); return st; }
+    for (size_t k = 0; k < count; ++k) outs[k] = tabs[k];
     return LVS_OK;
+}
+
+lvs_status lvs_preprocess(lvs_ctx *ctx, const lvs_ct_string *enc, const uint8_t *subset, size_t nsub,
+                          lvs_eq_table **out)
+{
+    if (!ctx || !out || !enc) return set_error(LVS_ERR_ARG, "lvs_preprocess: NULL argument");
+    return lvs_preprocess_batch(ctx, &enc, 1, subset, nsub, out);
 }
 
 void lvs_eq_table_free(lvs_eq_table *t)

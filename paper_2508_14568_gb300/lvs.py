@@ -35,7 +35,7 @@ EXPORTS = [
     "lvs_poly_mul_device", "lvs_ctx_set_timing", "lvs_ctx_kernel_stats", "lvs_ctx_pbs_count",
     "lvs_ctx_launch_count", "lvs_ct_string_upload", "lvs_pbs_batch_device_noalloc",
     "lvs_ctx_prepare_fft64", "lvs_pbs_batch_device_fft64", "lvs_noise_budget", "lvs_noise_plan",
-    "lvs_ctx_autotune", "lvs_ctx_ks_plan", "lvs_ctx_set_ks_plan", "lvs_probe_int_mul",
+    "lvs_ctx_autotune", "lvs_ctx_ks_plan", "lvs_ctx_set_ks_plan", "lvs_probe_int_mul", "lvs_preprocess_batch",
     "lvs_server_create", "lvs_server_submit", "lvs_server_poll", "lvs_server_stats_get", "lvs_server_free",
 ]
 
@@ -134,6 +134,7 @@ def _declare(L):
         "lvs_pbs_batch_device_fft64": ([vp, vp, sz, vp, vp, sz, sz], i32),
         "lvs_ctx_prepare_fft64": ([vp, vp], i32),
         "lvs_ctx_autotune": ([vp], i32),
+        "lvs_preprocess_batch": ([vp, vpp, sz, ctypes.c_char_p, sz, vpp], i32),
         "lvs_probe_int_mul": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
         "lvs_ctx_ks_plan": ([vp, sz, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "lvs_ctx_set_ks_plan": ([vp, sz, i32, i32], i32),
@@ -415,6 +416,15 @@ def lvs_preprocess(ctx, enc, subset=None):
     sb = _bytes(subset) if subset is not None else None
     _check(lib().lvs_preprocess(ctx, enc, sb, len(sb) if sb is not None else 0, ctypes.byref(out)))
     return EqTable(out.value, owner=ctx)
+
+
+def lvs_preprocess_batch(ctx, encs, subset=None):
+    n = len(encs)
+    E = (ctypes.c_void_p * max(1, n))(*[e.ptr for e in encs])
+    outs = (ctypes.c_void_p * max(1, n))()
+    sb = _bytes(subset) if subset is not None else None
+    _check(lib().lvs_preprocess_batch(ctx, E, n, sb, len(sb) if sb is not None else 0, outs))
+    return [EqTable(outs[k], owner=ctx) for k in range(n)]
 
 
 def lvs_edit_distance_preprocessed_batch(ctx, tables, plains, opts=None):

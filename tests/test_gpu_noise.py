@@ -105,3 +105,47 @@ def test_failure_rate_of_increasingly_noisy_ciphertexts():
     # errors grow with the noise
     assert rows[-1][1] > rows[0][1]
     L.lvs_ctx_free(ctx)
+
+
+def test_dp_noise_growth_matches_model():
+    """Section 3.1.3 on real ciphertexts: the phase error of the last-row
+    differences h[m][j] of long DNA pairs (full parameters) grows as the
+    oracle's noise tracker predicts (h[m][j] carries 2j - 1 PBS-output
+    variances for m >= j).  The errors, scaled by their predicted standard
+    deviation, must have unit variance."""
+    from oracle import noise as Nz
+    from oracle import plain as P
+    from paper_2508_14568_gb300 import workloads as W
+    import random
+
+    p = L.lvs_params_default()
+    ck, sk = L.lvs_keygen(p, 13)
+    ctx = L.lvs_ctx_create(sk, 0)
+    lwe_key, glwe_key = L.lvs_client_key_export(ck)
+    big = p.k * p.N
+    rng = random.Random(17)
+    m = 128
+    pairs = []
+    for _ in range(4):
+        a = "".join(rng.choice(W.DNA) for _ in range(m))
+        pairs.append((a, W.mutate_rate(rng, a, W.DNA, 0.10)[:m].ljust(m, "A")))
+    A = [L.lvs_encrypt_string(ck, a, L.LVS_ALPHA_DNA4, 21, 2 * k) for k, (a, b) in enumerate(pairs)]
+    B = [L.lvs_encrypt_string(ck, b, L.LVS_ALPHA_DNA4, 21, 2 * k + 1) for k, (a, b) in enumerate(pairs)]
+    r = L.lvs_edit_distance_batch(ctx, A, B)
+    var_pbs = predicted_pbs_variance(p, lwe_key, glwe_key)
+    pred = Nz.output_variances(m, m)
+    mask = glwe_key.astype(bool)
+    z = []
+    for k, (a, b) in enumerate(pairs):
+        rows = L.lvs_result_export(r, k, big)
+        _, h, _, _ = P.lvs_plain(a, b, P.ALPHA_DNA4)
+        phase = rows[:, big] - rows[:, :big][:, mask].sum(axis=1, dtype=np.uint64)
+        want = np.array([h[m][j] for j in range(1, m + 1)], dtype=np.uint64) << np.uint64(59)
+        err = (phase - want).view(np.int64).astype(np.float64)
+        sd = np.sqrt(np.array([pred[(m, j)][1] for j in range(1, m + 1)]) * var_pbs)
+        z.append(err / sd)
+    z = np.concatenate(z)
+    ratio = float(np.mean(z ** 2))
+    print("DP noise growth: %d samples, measured / predicted variance %.3f" % (z.size, ratio))
+    assert 0.8 < ratio < 1.2
+    L.lvs_ctx_free(ctx)

@@ -216,10 +216,20 @@ def test_full_params_one_cell_chain_bit_exact(full):
     assert d == [0]
 
 
-def test_config1_full_params_distance(full):
+def test_config1_full_params_bit_exact(full):
+    """Config 1 end to end at the full parameter set: the 48 PBS (16 EQ1, 16
+    EQ9, 16 cells) feed one another, so the encrypted last row equal to the
+    oracle's bit for bit means every PBS of the chain was; distance = WF."""
+    S = full
     pairs = W.config1()
-    r, d = _gpu_batch(full, pairs, P.ALPHA_ASCII7, seed=0)
+    r, d = _gpu_batch(S, pairs, P.ALPHA_ASCII7, seed=0)
     assert d == [P.wf_distance(a, b) for a, b in pairs]
+    a, b = pairs[0]
+    xa = T.encrypt_string(S.K, a, P.ALPHA_ASCII7, 0, 0)
+    yb = T.encrypt_string(S.K, b, P.ALPHA_ASCII7, 0, 1)
+    res = T.lvs_encrypted(S.K, xa, yb, P.ALPHA_ASCII7, parallel=True)
+    assert res["pbs"] == 48
+    assert np.array_equal(L.lvs_result_export(r, 0, S.big), np.stack(res["h_row"]))
 
 
 # ----------------------------------------------------------------- equality and preprocessing
@@ -286,6 +296,27 @@ def test_preprocess_table_bit_exact(small):
             v[(i, j)] = M - h[(i - 1, j)]
             h[(i, j)] = M - v[(i, j - 1)]
     assert np.array_equal(L.lvs_result_export(r, 0, S.big), np.stack([h[(m, j)] for j in range(1, n + 1)]))
+
+
+def test_preprocess_batch_equals_single_tables(small):
+    """Section 5 offline phase for many strings at once (one set of launches):
+    the online results from batched tables equal those from per-string tables
+    bit for bit, for ASCII / 27-symbol (two lookups) and DNA (one lookup)."""
+    S = small
+    for alpha, abc, pool in [(L.LVS_ALPHA_27, "AB EZ", W.ALPHA27[:6]), (L.LVS_ALPHA_DNA4, None, W.DNA)]:
+        rng = np.random.default_rng(5)
+        strs = ["".join(pool[x] for x in rng.integers(0, len(pool), size=int(rng.integers(1, 8)))) for _ in range(5)]
+        plains = ["".join(pool[x] for x in rng.integers(0, len(pool), size=int(rng.integers(1, 8)))) for _ in range(5)]
+        if abc is not None:
+            plains = ["".join(c for c in p if c in abc) or abc[0] for p in plains]
+        encs = [L.lvs_encrypt_string(S.ck, a, alpha, 73, k) for k, a in enumerate(strs)]
+        single = [L.lvs_preprocess(S.ctx, e, abc) for e in encs]
+        batch = L.lvs_preprocess_batch(S.ctx, encs, abc)
+        r1 = L.lvs_edit_distance_preprocessed_batch(S.ctx, single, plains)
+        r2 = L.lvs_edit_distance_preprocessed_batch(S.ctx, batch, plains)
+        for k in range(len(strs)):
+            assert np.array_equal(L.lvs_result_export(r1, k, S.big), L.lvs_result_export(r2, k, S.big))
+        assert L.lvs_decrypt_all(S.ck, r2) == [P.wf_distance(a, b) for a, b in zip(strs, plains)]
 
 
 def test_config2_full_size_distances(full):

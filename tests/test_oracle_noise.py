@@ -163,3 +163,13 @@ def test_budget_and_pfail_consistent():
     # the configurations (at most 256 characters) stay far inside the budget
     assert Nz.key_variance_closed_form(256, 256) < b
     assert Nz.pfail_of(p, 14 * 255 + 10) < 2.0 ** -80
+
+
+def test_output_variances_closed_form():
+    """dv_out = M - dh_in and dh_out = M - dv_in: along the diagonal each step
+    adds two unit terms, so for a full matrix var h[i][j] = 2j - 1 (i >= j) or
+    2i (i < j), and var v[i][j] = 2i - 1 (j >= i) or 2j (j < i)."""
+    out = Nz.output_variances(9, 7)
+    for (i, j), (vv, vh) in out.items():
+        assert vh == (2 * j - 1 if i >= j else 2 * i)
+        assert vv == (2 * i - 1 if j >= i else 2 * j)
