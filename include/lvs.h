@@ -147,6 +147,11 @@ lvs_status lvs_ct_string_import(const uint64_t *src, size_t len, lvs_alphabet al
  * the device copy instead of uploading.  Synchronous.  Calling it again is a
  * no-op. */
 lvs_status lvs_ct_string_upload(lvs_ctx *ctx, lvs_ct_string *s);
+/* Keeps a page-locked (pinned) host copy of the ciphertexts, freed with the
+ * string; later host-to-device copies of the string (batch calls on host
+ * strings, lvs_ct_string_upload) read it, so they run as asynchronous DMA.
+ * Calling it again is a no-op. */
+lvs_status lvs_ct_string_pin(lvs_ct_string *s);
 
 /* Decrypts one big LWE ciphertext to its Z_32 plaintext (round(phase/2^59)). */
 lvs_status lvs_decrypt_lwe(const lvs_client_key *ck, const uint64_t *ct, uint32_t *value);

@@ -341,6 +341,10 @@ lvs_status lvs_encrypt_string(const lvs_client_key *ck, const uint8_t *s, size_t
 void lvs_ct_string_free(lvs_ct_string *s)
 {
     if (!s) return;
+    if (s->pinned) {
+        cudaFreeHost(s->pinned);
+        cudaGetLastError();
+    }
     if (s->d) {
         int cur = 0;
         cudaGetDevice(&cur);

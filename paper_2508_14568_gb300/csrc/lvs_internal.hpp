@@ -92,6 +92,8 @@ struct lvs_ct_string {
     uint64_t *d = nullptr;       // optional device copy, rows of `dstride` words
     size_t dstride = 0;
     int ddevice = -1;
+    uint64_t *pinned = nullptr;  // optional page-locked copy of `data` (lvs_ct_string_pin)
+    const uint64_t *host() const { return pinned ? pinned : data.data(); }
 };
 
 namespace lvs {

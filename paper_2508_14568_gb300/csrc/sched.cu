@@ -47,7 +47,7 @@ lvs_status upload_string(lvs_ctx *ctx, const lvs_ct_string *s, const Arena &A, s
     const size_t nrows = s->len * s->symbols;
     if (nrows == 0) return LVS_OK;
     const size_t w = (size_t)s->big + 1;
-    LVS_CUDA(cudaMemcpy2DAsync(A.row(first), A.stride * 8, s->data.data(), w * 8, w * 8, nrows,
+    LVS_CUDA(cudaMemcpy2DAsync(A.row(first), A.stride * 8, s->host(), w * 8, w * 8, nrows,
                                cudaMemcpyHostToDevice, ctx->stream));
     return LVS_OK;
 }
@@ -331,10 +331,10 @@ lvs_status lvs_eq(lvs_ctx *ctx, const lvs_ct_string *a, size_t i, const lvs_ct_s
     // rows: x (C), y (C), eq1
     if ((st = arena_alloc(ctx, 2 * C + 1, A)) != LVS_OK) return st;
     const size_t w = (size_t)a->big + 1;
-    cudaError_t e = cudaMemcpy2DAsync(A.row(0), A.stride * 8, a->data.data() + i * C * w, w * 8, w * 8, C,
+    cudaError_t e = cudaMemcpy2DAsync(A.row(0), A.stride * 8, a->host() + i * C * w, w * 8, w * 8, C,
                                       cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(A.row(C), A.stride * 8, b->data.data() + j * C * w, w * 8, w * 8, C,
+        e = cudaMemcpy2DAsync(A.row(C), A.stride * 8, b->host() + j * C * w, w * 8, w * 8, C,
                               cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) { arena_free(ctx, A); return cuda_error(e, "lvs_eq upload"); }
     lvs_result *r = nullptr;
@@ -538,6 +538,20 @@ lvs_status lvs_edit_distance_preprocessed_batch(lvs_ctx *ctx, const lvs_eq_table
     return LVS_OK;
 }
 
+lvs_status lvs_ct_string_pin(lvs_ct_string *s)
+{
+    if (!s) return set_error(LVS_ERR_ARG, "lvs_ct_string_pin: NULL string");
+    if (s->pinned || s->data.empty()) return LVS_OK;
+    uint64_t *h = nullptr;
+    if (cudaMallocHost((void **)&h, s->data.size() * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(LVS_ERR_OOM, "lvs_ct_string_pin: page-locked allocation failed");
+    }
+    memcpy(h, s->data.data(), s->data.size() * 8);
+    s->pinned = h;
+    return LVS_OK;
+}
+
 lvs_status lvs_ct_string_upload(lvs_ctx *ctx, lvs_ct_string *s)
 {
     if (!ctx || !s) return set_error(LVS_ERR_ARG, "lvs_ct_string_upload: NULL argument");
@@ -554,7 +568,7 @@ lvs_status lvs_ct_string_upload(lvs_ctx *ctx, lvs_ct_string *s)
         cudaGetLastError();
         return set_error(LVS_ERR_OOM, "lvs_ct_string_upload: device allocation failed");
     }
-    cudaError_t e = cudaMemcpy2D(d, stride * 8, s->data.data(), w * 8, w * 8, rows, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy2D(d, stride * 8, s->host(), w * 8, w * 8, rows, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(d); return cuda_error(e, "lvs_ct_string_upload"); }
     s->d = d;
     s->dstride = stride;

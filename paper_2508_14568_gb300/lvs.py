@@ -36,6 +36,7 @@ EXPORTS = [
     "lvs_ctx_launch_count", "lvs_ct_string_upload", "lvs_pbs_batch_device_noalloc",
     "lvs_ctx_prepare_fft64", "lvs_pbs_batch_device_fft64", "lvs_noise_budget", "lvs_noise_plan",
     "lvs_ctx_autotune", "lvs_ctx_ks_plan", "lvs_ctx_set_ks_plan", "lvs_probe_int_mul", "lvs_preprocess_batch",
+    "lvs_ct_string_pin",
     "lvs_server_create", "lvs_server_submit", "lvs_server_poll", "lvs_server_stats_get", "lvs_server_free",
 ]
 
@@ -134,6 +135,7 @@ def _declare(L):
         "lvs_pbs_batch_device_fft64": ([vp, vp, sz, vp, vp, sz, sz], i32),
         "lvs_ctx_prepare_fft64": ([vp, vp], i32),
         "lvs_ctx_autotune": ([vp], i32),
+        "lvs_ct_string_pin": ([vp], i32),
         "lvs_preprocess_batch": ([vp, vpp, sz, ctypes.c_char_p, sz, vpp], i32),
         "lvs_probe_int_mul": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
         "lvs_ctx_ks_plan": ([vp, sz, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
@@ -351,6 +353,10 @@ def lvs_encrypt_string(ck, s, alphabet, noise_seed, string_id):
     out = ctypes.c_void_p()
     _check(lib().lvs_encrypt_string(ck, b, len(b), alphabet, noise_seed, string_id, ctypes.byref(out)))
     return CtString(out.value)
+
+
+def lvs_ct_string_pin(s):
+    _check(lib().lvs_ct_string_pin(s))
 
 
 def lvs_ct_string_upload(ctx, s):

@@ -194,6 +194,21 @@ def test_edit_distance_dna_ciphertexts_bit_exact(small):
     assert d == [P.wf_distance(a, b) for a, b in pairs]
 
 
+def test_pinned_host_strings_identical(small):
+    S = small
+    pairs = W.random_pairs(29, 6, W.PRINTABLE, 1, 9)
+    A = [L.lvs_encrypt_string(S.ck, a, L.LVS_ALPHA_ASCII7, 54, 2 * k) for k, (a, b) in enumerate(pairs)]
+    B = [L.lvs_encrypt_string(S.ck, b, L.LVS_ALPHA_ASCII7, 54, 2 * k + 1) for k, (a, b) in enumerate(pairs)]
+    r1 = L.lvs_edit_distance_batch(S.ctx, A, B)
+    for s in A + B:
+        L.lvs_ct_string_pin(s)
+        L.lvs_ct_string_pin(s)       # no-op
+    r2 = L.lvs_edit_distance_batch(S.ctx, A, B)
+    for k in range(len(pairs)):
+        assert np.array_equal(L.lvs_result_export(r1, k, S.big), L.lvs_result_export(r2, k, S.big))
+    assert L.lvs_decrypt_all(S.ck, r2) == [P.wf_distance(a, b) for a, b in pairs]
+
+
 def test_graph_and_direct_launches_identical(small):
     pairs = W.random_pairs(23, 12, W.PRINTABLE, 1, 9)
     r1, d1 = _gpu_batch(small, pairs, P.ALPHA_ASCII7, use_graph=True)
