@@ -298,6 +298,7 @@ def run_lvs(args):
     # key-switch launch shapes by measurement (before any timing)
     L.lvs_ctx_autotune(ctx)
     ks_plans = {str(nj): list(L.lvs_ctx_ks_plan(ctx, nj)) for nj in (4, 16, 64, 256, 1024, 4096)}
+    br_split = L.lvs_ctx_br_split(ctx)
     big = params.k * params.N
     cells = sum(len(a) * len(b) for a, b in pairs)
     want = [P.wf_distance(a, b) for a, b in pairs]
@@ -488,7 +489,8 @@ def run_lvs(args):
                          if achieved else None},
             "kernels": {"blind_rotate": br, "keyswitch": ks,
                         "ks_plans": {"note": "launch size bucket end -> [PBS per CTA, split] (lvs_ctx_autotune)",
-                                     "plans": ks_plans}},
+                                     "plans": ks_plans},
+                        "br_three_cta_max_pbs": br_split},
             "latency_ms": {"p50": batched_latency_ms, "p99": batched_latency_ms,
                            "note": "batched: all pairs of a step complete together"},
             "one_pair_at_a_time": serial,

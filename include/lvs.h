@@ -366,11 +366,13 @@ lvs_status lvs_pbs_batch_device_noalloc(lvs_ctx *ctx, const uint64_t *d_in, size
                                         const uint8_t *d_lut, uint64_t *d_out, size_t out_stride,
                                         size_t count);
 
-/* Autotuner of the key-switch launch shape (no counterpart in the paper):
- * for each launch-size bucket (1-4, 5-16, 17-64, 65-256, 257-1024, more
+/* Autotuner of the launch shapes (no counterpart in the paper): for each
+ * key-switch launch-size bucket (1-4, 5-16, 17-64, 65-256, 257-1024, more
  * PBS per launch) it times every candidate plan -- 4 or 16 PBS per CTA,
  * the 2048 input coefficients split over 1..32 CTAs with a finishing
- * reduction -- on synthetic jobs and keeps the fastest in the context.
+ * reduction -- on synthetic jobs and keeps the fastest in the context; for
+ * the blind rotation it finds the largest launch size for which the
+ * three-CTA form (lvs_ctx_set_br_split) is faster.
  * Without it a heuristic plan is used (fill about two CTAs per SM).  Every
  * plan gives the same result bit for bit.  Synchronous; takes about a second;
  * allocates and frees its own scratch. */
@@ -380,6 +382,14 @@ lvs_status lvs_ctx_ks_plan(lvs_ctx *ctx, size_t njobs, int32_t *jobs_per_cta, in
 /* Forces the plan of njobs' bucket (jobs_per_cta 4 or 16, split 1..32;
  * jobs_per_cta 0 restores the heuristic).  For tests and experiments. */
 lvs_status lvs_ctx_set_ks_plan(lvs_ctx *ctx, size_t njobs, int32_t jobs_per_cta, int32_t split);
+/* Blind-rotation launches of at most max_jobs PBS run as one cluster of three
+ * CTAs per ciphertext (one per NTT prime, residues exchanged through
+ * distributed shared memory): lower latency when the launch leaves SMs idle.
+ * The default is one ciphertext per three SMs; lvs_ctx_autotune measures the
+ * crossover.  Same results bit for bit.  lvs_ctx_set_br_split(ctx, 0) turns it
+ * off; LVS_ERR_STATE if the device cannot run it. */
+lvs_status lvs_ctx_br_split(lvs_ctx *ctx, size_t *max_jobs);
+lvs_status lvs_ctx_set_br_split(lvs_ctx *ctx, size_t max_jobs);
 
 /* Measured issue rate of 32-bit integer multiplies on `device`: low-half
  * (mul.lo / IMAD) and high-half (mul.hi) results per SM per clock, from one

@@ -226,6 +226,10 @@ lvs_status lvs_ctx_create(const lvs_server_key *sk, int device, void *stream, lv
     if (e == cudaSuccess) e = prepare_kernels(N);
     if (e != cudaSuccess) return fail(cuda_error(e, "kernel setup"));
     ctx->br_grid = std::max(1, ctx->num_sms * std::max(1, br_blocks_per_sm(N)));
+    // three-CTA blind rotation for launches that leave SMs idle: by default up
+    // to one ciphertext per three SMs (lvs_ctx_autotune measures the crossover)
+    ctx->br_clusters = br_cluster_capacity(N);
+    ctx->br_split_max = ctx->br_clusters > 0 ? (size_t)(ctx->num_sms / 3) : 0;
 
     std::vector<uint32_t> tw;
     make_twiddles(N, tw);

@@ -10,6 +10,8 @@
 #include <algorithm>
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "lvs_internal.hpp"
 #include "ntt.cuh"
 
@@ -42,10 +44,10 @@ __device__ __forceinline__ uint64_t test_poly_at(const uint8_t (&f)[16], uint32_
 // External product core for prime group g: digit residues d (L0 layout, in
 // [0, p)) -> forward NTT -> Montgomery products with the key slice `key`
 // ([16][T][8] u32 for this prime, this thread at +tau*8) -> inverse NTT ->
-// residues of the two output polynomials written to crt[(g*2+j)*N + e].
+// residues of the two output polynomials written to out[j*N + e].
 template <int LOGN>
 __device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][16], const uint32_t *__restrict__ key,
-                                                 uint32_t *buf, uint32_t *crt, uint32_t tau, int g,
+                                                 uint32_t *buf, uint32_t *out, uint32_t tau, int g,
                                                  const uint2 *__restrict__ twf, const uint2 *__restrict__ twi)
 {
     using Lay = Layout<LOGN>;
@@ -82,8 +84,68 @@ __device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][16], const uin
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         const uint32_t e = tau | ((uint32_t)q << Lay::B0);
-        crt[(g * 2 + 0) * N + e] = csub(d[0][q], p);
-        crt[(g * 2 + 1) * N + e] = csub(d[1][q], p);
+        out[0 * N + e] = csub(d[0][q], p);
+        out[1 * N + e] = csub(d[1][q], p);
+    }
+}
+
+// Digit residues (mod this group's prime) of X^a ACC - ACC at the 16 positions
+// of the thread in the L0 layout, for the mask (j = 0) and body (j = 1)
+// polynomials of the negacyclically extended accumulator acc ([2][2N]).
+// Only the rounded top 2*base_log bits of x are used: with
+// shift = 64 - 2*base_log >= 32, (x + 2^(shift-1)) >> shift =
+// (hi32(x) + 2^(shift-33)) >> (shift-32).  Balanced digits with carry,
+// least significant level first; d < 0 is stored as d + p (< 2p is fine).
+template <int LOGN>
+__device__ __forceinline__ void decompose(uint32_t (&d)[4][16], const uint64_t *acc, uint32_t a, uint32_t tau,
+                                          uint32_t base_log, uint32_t pmB)
+{
+    using Lay = Layout<LOGN>;
+    constexpr int N = Lay::N;
+    const uint32_t B = 1u << base_log, hB = B >> 1;
+    const uint32_t hshift = 64 - 2 * base_log - 32;   // shift - 32
+    const uint32_t hround = 1u << (hshift - 1);       // 2^(shift - 33)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const uint32_t e = tau | ((uint32_t)q << Lay::B0);
+        const uint32_t src = (e - a) & (2 * N - 1);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const uint64_t *A = acc + j * 2 * N;
+            const uint64_t x = A[src] - A[e];
+            const uint32_t v = ((uint32_t)(x >> 32) + hround) >> hshift;
+            const uint32_t u2 = v & (B - 1);
+            const uint32_t c2 = u2 >> (base_log - 1);   // u2 >= B/2
+            const uint32_t r1 = (v >> base_log) + c2;    // <= B
+            const uint32_t c1 = (r1 + hB) >> base_log;   // r1 >= B/2 (r1 = B gives 1)
+            d[2 * j + 1][q] = u2 + c2 * pmB;
+            d[2 * j + 0][q] = r1 + c1 * pmB;
+        }
+    }
+}
+
+// Sample extract (coefficient 0) of the extended accumulator and the job's
+// epilogue: a_0 = A[0], a_u = -A[N - u] = A[2N - u] (u > 0), b = B[0]; a cell
+// job updates v[i] = M - h[i-1][j], h[j] = M - v[i][j-1] in place (and copies
+// one of them to its tap row), a store job writes the ciphertext (and its tap).
+template <int LOGN>
+__device__ __forceinline__ void sample_extract_epilogue(const Job &J, const uint64_t *acc, int tid, int nthreads)
+{
+    constexpr int N = 1 << LOGN;
+    uint64_t *o0 = J.dst[0];
+    uint64_t *o1 = J.dst[1];
+    for (int u = tid; u <= N; u += nthreads) {
+        const uint64_t val = u == N ? acc[2 * N] : acc[(2 * N - u) & (2 * N - 1)];
+        if (J.kind == JOB_CELL) {
+            const uint64_t vold = o0[u], hold = o1[u];
+            const uint64_t vn = val - hold, hn = val - vold;
+            o0[u] = vn;
+            o1[u] = hn;
+            if (J.tapsel) J.tap[u] = J.tapsel == 1 ? vn : hn;
+        } else {
+            o0[u] = val;
+            if (J.tapsel) J.tap[u] = val;
+        }
     }
 }
 
@@ -117,9 +179,7 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
     const uint32_t p = c_pc.p[g];
     const uint2 *twf = tw + (size_t)(g * 2 + 0) * N;
     const uint2 *twi = tw + (size_t)(g * 2 + 1) * N;
-    const uint32_t B = 1u << base_log, hB = B >> 1, pmB = p - B;
-    const uint32_t hshift = 64 - 2 * base_log - 32;   // shift - 32
-    const uint32_t hround = 1u << (hshift - 1);       // 2^(shift - 33)
+    const uint32_t pmB = p - (1u << base_log);
     const size_t key_row = (size_t)3 * 16 * T * 8;   // u32 per BSK index i
 
     for (uint32_t job = blockIdx.x; job < njobs; job += gridDim.x) {
@@ -143,30 +203,10 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
         for (uint32_t i = 0; i < n; ++i) {
             const uint32_t a = __ldg(msj + i);
             if (a == 0) continue;   // X^0 ACC - ACC = 0: the external product is exactly 0
-            // digits of X^a ACC - ACC.  Only the rounded top 2*base_log bits of
-            // x are used: with shift = 64 - 2*base_log >= 32,
-            // (x + 2^(shift-1)) >> shift = (hi32(x) + 2^(shift-33)) >> (shift-32).
             uint32_t d[4][16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const uint32_t e = tau | ((uint32_t)q << Lay::B0);
-                const uint32_t src = (e - a) & (2 * N - 1);
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const uint64_t *A = acc + j * 2 * N;
-                    const uint64_t x = A[src] - A[e];
-                    const uint32_t v = ((uint32_t)(x >> 32) + hround) >> hshift;
-                    const uint32_t u2 = v & (B - 1);
-                    const uint32_t c2 = u2 >> (base_log - 1);   // u2 >= B/2
-                    const uint32_t r1 = (v >> base_log) + c2;    // <= B
-                    const uint32_t c1 = (r1 + hB) >> base_log;   // r1 >= B/2 (r1 = B gives 1)
-                    // residues of the balanced digits (d < 0 -> d + p; < 2p is fine)
-                    d[2 * j + 1][q] = u2 + c2 * pmB;
-                    d[2 * j + 0][q] = r1 + c1 * pmB;
-                }
-            }
-            ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 16 * T * 8, buf, crt, tau, g,
-                                   twf, twi);
+            decompose<LOGN>(d, acc, a, tau, base_log, pmB);
+            ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 16 * T * 8, buf, crt + g * 2 * N, tau,
+                                   g, twf, twi);
             __syncthreads();
             for (int c = tid; c < 2 * N; c += NT) {
                 const int j = c >> LOGN, e = c & (N - 1);
@@ -180,23 +220,7 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
             __syncthreads();
         }
 
-        // sample extract (coefficient 0) and epilogue: a_0 = A[0], a_u = -A[N - u]
-        // = A[2N - u] (u > 0), b = B[0]
-        uint64_t *o0 = J.dst[0];
-        uint64_t *o1 = J.dst[1];
-        for (int u = tid; u <= N; u += NT) {
-            const uint64_t val = u == N ? acc[2 * N] : acc[(2 * N - u) & (2 * N - 1)];
-            if (J.kind == JOB_CELL) {
-                const uint64_t vold = o0[u], hold = o1[u];
-                const uint64_t vn = val - hold, hn = val - vold;
-                o0[u] = vn;   // v[i][j] = M - h[i-1][j]
-                o1[u] = hn;   // h[i][j] = M - v[i][j-1]
-                if (J.tapsel) J.tap[u] = J.tapsel == 1 ? vn : hn;
-            } else {
-                o0[u] = val;
-                if (J.tapsel) J.tap[u] = val;
-            }
-        }
+        sample_extract_epilogue<LOGN>(J, acc, tid, NT);
         __syncthreads();
     }
 }
@@ -395,6 +419,97 @@ k_bsk_to_ntt(const uint64_t *__restrict__ coef, uint32_t count, uint32_t *__rest
     }
 }
 
+// ---------------------------------------------------------------- blind rotation, one PBS on three SMs
+// For launches too small to fill the GPU (latency): a cluster of three CTAs
+// per ciphertext, CTA g running prime g's transforms (the same per-thread work
+// as one prime group of k_blind_rotate), so a CMux takes one third of the SM
+// work.  Each CTA keeps its own copy of the accumulator; after the inverse
+// transforms the residues are exchanged through distributed shared memory:
+// CTA g reconstructs every third block of coefficients from the three CTAs'
+// residues and writes the new values into all three accumulator copies.  Two
+// cluster barriers per CMux (residues ready; accumulators updated).  All CTAs
+// of a cluster run the same jobs and the same CMux sequence, so every CTA
+// reaches every cluster barrier.
+template <int LOGN>
+struct BrClSmem {
+    static constexpr int N = 1 << LOGN;
+    static constexpr size_t acc_bytes = 2 * 2 * N * sizeof(uint64_t);
+    static constexpr size_t buf_bytes = 4 * N * sizeof(uint32_t);
+    static constexpr size_t res_bytes = 2 * N * sizeof(uint32_t);
+    static constexpr size_t total = acc_bytes + buf_bytes + res_bytes;
+};
+
+template <int LOGN>
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__((1 << LOGN) / 16, 2)
+k_blind_rotate_cl(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__restrict__ ms, uint32_t n,
+                  const uint32_t *__restrict__ bsk, const uint2 *__restrict__ tw, const uint8_t *__restrict__ luts,
+                  int lut_per_job, uint32_t base_log)
+{
+    namespace cg = cooperative_groups;
+    using Lay = Layout<LOGN>;
+    constexpr int N = Lay::N, T = Lay::T;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    uint64_t *acc = reinterpret_cast<uint64_t *>(smem_raw);
+    uint32_t *buf = reinterpret_cast<uint32_t *>(smem_raw + BrClSmem<LOGN>::acc_bytes);
+    uint32_t *res = buf + 4 * N;                 // this prime's residues [2][N]
+
+    const int g = (int)cl.block_rank();
+    const uint32_t tau = threadIdx.x;
+    const uint32_t p = c_pc.p[g];
+    const uint2 *twf = tw + (size_t)(g * 2 + 0) * N;
+    const uint2 *twi = tw + (size_t)(g * 2 + 1) * N;
+    const uint32_t pmB = p - (1u << base_log);
+    const size_t key_row = (size_t)3 * 16 * T * 8;
+    const uint32_t *res_of[3];
+    uint64_t *acc_of[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        res_of[r] = cl.map_shared_rank(res, r);
+        acc_of[r] = cl.map_shared_rank(acc, r);
+    }
+    const uint32_t nclusters = gridDim.x / 3, cid = blockIdx.x / 3;
+
+    for (uint32_t job = cid; job < njobs; job += nclusters) {
+        const Job J = jobs[job];
+        const uint32_t *msj = ms + (size_t)job * (n + 1);
+        uint8_t f[16];
+        {
+            const uint8_t *lp = luts + (lut_per_job ? (size_t)job * 16 : (size_t)J.lut * 16);
+            const uint4 lv = *reinterpret_cast<const uint4 *>(lp);
+            memcpy(f, &lv, 16);
+        }
+        const uint32_t b = __ldg(msj + n);
+        for (int t = tau; t < 2 * N; t += T) {
+            acc[t] = 0;
+            acc[2 * N + t] = test_poly_at<LOGN>(f, (t + b) & (2 * N - 1));
+        }
+        __syncthreads();
+        for (uint32_t i = 0; i < n; ++i) {
+            const uint32_t a = __ldg(msj + i);
+            if (a == 0) continue;   // the same for the three CTAs
+            uint32_t d[4][16];
+            decompose<LOGN>(d, acc, a, tau, base_log, pmB);
+            ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 16 * T * 8, buf, res, tau, g, twf,
+                                   twi);
+            cl.sync();   // the three primes' residues are in place
+            for (int c = g * T + (int)tau; c < 2 * N; c += 3 * T) {
+                const int j = c >> LOGN, e = c & (N - 1);
+                const uint64_t x = crt3(res_of[0][j * N + e], res_of[1][j * N + e], res_of[2][j * N + e], c_pc);
+                const uint64_t y = acc[j * 2 * N + e] + x;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    acc_of[r][j * 2 * N + e] = y;
+                    acc_of[r][j * 2 * N + e + N] = 0 - y;
+                }
+            }
+            cl.sync();   // every copy of the accumulator is updated; residues may be overwritten
+        }
+        if (g == 0) sample_extract_epilogue<LOGN>(J, acc, (int)tau, T);
+        __syncthreads();
+    }
+}
+
 // Product-only kernel (parity of the NTT/CRT path): out[item] = sum_r dig[r] * key[r][col]
 template <int LOGN>
 __global__ void __launch_bounds__(3 * (1 << LOGN) / 16, 1)
@@ -421,7 +536,8 @@ k_poly_mul(const int32_t *__restrict__ dig, const uint32_t *__restrict__ keyntt,
             d[r][q] = x < 0 ? (uint32_t)(x + (int32_t)p) : (uint32_t)x;
         }
     ext_product_core<LOGN>(d, keyntt + (size_t)item * 3 * 16 * T * 8 + (size_t)g * 16 * T * 8,
-                           bufs + g * 4 * N, crt, tau, g, tw + (size_t)(g * 2) * N, tw + (size_t)(g * 2 + 1) * N);
+                           bufs + g * 4 * N, crt + g * 2 * N, tau, g, tw + (size_t)(g * 2) * N,
+                           tw + (size_t)(g * 2 + 1) * N);
     __syncthreads();
     for (int c = tid; c < 2 * N; c += NT) {
         const int j = c >> LOGN, e = c & (N - 1);
@@ -460,9 +576,36 @@ static cudaError_t set_attrs()
     e = cudaFuncSetAttribute(k_poly_mul<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)BrSmem<LOGN>::total);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_blind_rotate_cl<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BrClSmem<LOGN>::total);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_bsk_to_ntt<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(3 * 4 * (1 << LOGN) * sizeof(uint32_t)));
 }
+
+template <int LOGN>
+static int max_clusters()
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(3, 1, 1);
+    cfg.blockDim = dim3((1 << LOGN) / 16, 1, 1);
+    cfg.dynamicSmemBytes = BrClSmem<LOGN>::total;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 3;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k_blind_rotate_cl<LOGN>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc;
+}
+
+int br_cluster_capacity(uint32_t N) { return N == 2048 ? max_clusters<11>() : max_clusters<9>(); }
 
 cudaError_t prepare_kernels(uint32_t N) { return N == 2048 ? set_attrs<11>() : set_attrs<9>(); }
 
@@ -554,8 +697,19 @@ cudaError_t launch_blind_rotate(const lvs_ctx *ctx, const Job *jobs, size_t njob
 {
     if (njobs == 0) return cudaSuccess;
     const auto &p = ctx->P.p;
-    const unsigned grid = (unsigned)std::min<size_t>(njobs, (size_t)ctx->br_grid);
     const uint2 *t2 = reinterpret_cast<const uint2 *>(ctx->tw);
+    if (njobs <= ctx->br_split_max && ctx->br_clusters > 0) {
+        // small launch: one ciphertext per cluster of three CTAs (one per prime)
+        const unsigned grid = 3 * (unsigned)std::min<size_t>(njobs, (size_t)ctx->br_clusters);
+        if (p.N == 2048)
+            k_blind_rotate_cl<11><<<grid, (1 << 11) / 16, BrClSmem<11>::total, s>>>(
+                jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log);
+        else
+            k_blind_rotate_cl<9><<<grid, (1 << 9) / 16, BrClSmem<9>::total, s>>>(
+                jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log);
+        return cudaGetLastError();
+    }
+    const unsigned grid = (unsigned)std::min<size_t>(njobs, (size_t)ctx->br_grid);
     if (p.N == 2048)
         k_blind_rotate<11><<<grid, br_threads(p.N), BrSmem<11>::total, s>>>(
             jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log);

@@ -137,6 +137,8 @@ struct lvs_ctx {
     bool own_stream = false;
     int num_sms = 0;
     int br_grid = 0;
+    int br_clusters = 0;           // resident clusters of the three-CTA blind rotation
+    size_t br_split_max = 0;       // launches of at most this many PBS use it (0: never)
     // device keys
     uint32_t *bsk_ntt = nullptr;   // [n][kPrimes][16][T][8] u32
     uint64_t *ksk = nullptr;       // [kN][ks_l][n+1]
@@ -209,6 +211,7 @@ cudaError_t launch_poly_mul(const lvs_ctx *ctx, const int32_t *dig, const uint32
 cudaError_t launch_fill_trivial(uint64_t *arena, size_t stride, uint32_t big, size_t first, size_t count,
                                 uint64_t body, cudaStream_t s);
 int br_smem_bytes(uint32_t N);
+int br_cluster_capacity(uint32_t N);
 int br_threads(uint32_t N);
 size_t bsk_ntt_words(uint32_t n, uint32_t N);
 

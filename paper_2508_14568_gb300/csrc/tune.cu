@@ -1,5 +1,7 @@
-// Autotuner of the key-switch launch shape (jobs per CTA and split of the
-// input coefficients over CTAs), per launch-size bucket.
+// Autotuner of the launch shapes: the key switch's (jobs per CTA and split
+// of the input coefficients over CTAs, per launch-size bucket) and the blind
+// rotation's (one CTA per ciphertext, or three -- one per prime -- for small
+// launches).
 //
 // Small launches (one pair's first anti-diagonals, a lone query) leave most
 // SMs idle with one CTA column block per 16 jobs; splitting the 2048 input
@@ -108,6 +110,57 @@ lvs_status lvs_ctx_autotune(lvs_ctx *ctx)
         }
         if (st == LVS_OK) ctx->ks_tuned[b] = best;
     }
+    // blind rotation: one CTA per ciphertext vs three CTAs (one per prime) per
+    // ciphertext, on synthetic jobs (rotation amounts from a byte pattern);
+    // the three-CTA form is kept up to the largest tested launch size where it
+    // is faster, scanning upwards
+    if (st == LVS_OK && ctx->br_clusters > 0) {
+        const size_t nmax = 2 * (size_t)ctx->num_sms;
+        uint64_t *dst = nullptr;
+        if (cudaMalloc((void **)&dst, nmax * row * 8) != cudaSuccess) {
+            cudaGetLastError();
+            cleanup();
+            return set_error(LVS_ERR_OOM, "lvs_ctx_autotune: device allocation failed");
+        }
+        std::vector<Job> bj(nmax);
+        for (size_t k = 0; k < nmax; ++k) {
+            memset(&bj[k], 0, sizeof(Job));
+            bj[k].kind = JOB_STORE;
+            bj[k].lut = LUT_MIN;
+            bj[k].dst[0] = dst + k * row;
+        }
+        cudaError_t e2 = cudaMemcpyAsync(djobs, bj.data(), nmax * sizeof(Job), cudaMemcpyHostToDevice, ctx->stream);
+        if (e2 == cudaSuccess) e2 = cudaMemsetAsync(ms, 0x35, nmax * (p.n + 1) * 4, ctx->stream);
+        if (e2 != cudaSuccess) st = cuda_error(e2, "lvs_ctx_autotune: blind-rotation set-up");
+        const size_t keep = ctx->br_split_max;
+        size_t best_max = 0;
+        const size_t sizes[] = {1, 8, 24, (size_t)ctx->num_sms / 3, (size_t)ctx->num_sms / 2,
+                                (size_t)(2 * ctx->num_sms) / 3, (size_t)ctx->num_sms};
+        for (size_t nj : sizes) {
+            if (st != LVS_OK || nj == 0 || nj > nmax) break;
+            float t[2] = {0, 0};
+            for (int form = 0; form < 2 && st == LVS_OK; ++form) {
+                ctx->br_split_max = form == 1 ? nj : 0;
+                float best_t = 1e30f;
+                for (int rep = 0; rep < 3 && st == LVS_OK; ++rep) {
+                    cudaError_t e3 = cudaEventRecord(e0, ctx->stream);
+                    if (e3 == cudaSuccess) e3 = launch_blind_rotate(ctx, djobs, nj, ms, ctx->luts, 0, ctx->stream);
+                    if (e3 == cudaSuccess) e3 = cudaEventRecord(e1, ctx->stream);
+                    if (e3 == cudaSuccess) e3 = cudaEventSynchronize(e1);
+                    float ms_ = 0;
+                    if (e3 == cudaSuccess) e3 = cudaEventElapsedTime(&ms_, e0, e1);
+                    if (e3 != cudaSuccess) st = cuda_error(e3, "lvs_ctx_autotune: blind-rotation timing");
+                    else if (rep > 0) best_t = std::min(best_t, ms_);
+                }
+                t[form] = best_t;
+            }
+            if (st != LVS_OK || t[1] >= t[0]) break;
+            best_max = nj;
+        }
+        ctx->br_split_max = st == LVS_OK ? best_max : keep;
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(dst);
+    }
     cleanup();
     return st;
 }
@@ -118,6 +171,22 @@ lvs_status lvs_ctx_ks_plan(lvs_ctx *ctx, size_t njobs, int32_t *jobs_per_cta, in
     const KsPlan pl = ks_plan(ctx, njobs);
     *jobs_per_cta = pl.tj;
     *split = pl.split;
+    return LVS_OK;
+}
+
+lvs_status lvs_ctx_br_split(lvs_ctx *ctx, size_t *max_jobs)
+{
+    if (!ctx || !max_jobs) return set_error(LVS_ERR_ARG, "lvs_ctx_br_split: NULL argument");
+    *max_jobs = ctx->br_clusters > 0 ? ctx->br_split_max : 0;
+    return LVS_OK;
+}
+
+lvs_status lvs_ctx_set_br_split(lvs_ctx *ctx, size_t max_jobs)
+{
+    if (!ctx) return set_error(LVS_ERR_ARG, "lvs_ctx_set_br_split: NULL context");
+    if (max_jobs > 0 && ctx->br_clusters <= 0)
+        return set_error(LVS_ERR_STATE, "lvs_ctx_set_br_split: the device cannot run the three-CTA form");
+    ctx->br_split_max = max_jobs;
     return LVS_OK;
 }
 

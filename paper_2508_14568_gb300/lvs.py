@@ -36,7 +36,7 @@ EXPORTS = [
     "lvs_ctx_launch_count", "lvs_ct_string_upload", "lvs_pbs_batch_device_noalloc",
     "lvs_ctx_prepare_fft64", "lvs_pbs_batch_device_fft64", "lvs_noise_budget", "lvs_noise_plan",
     "lvs_ctx_autotune", "lvs_ctx_ks_plan", "lvs_ctx_set_ks_plan", "lvs_probe_int_mul", "lvs_preprocess_batch",
-    "lvs_ct_string_pin",
+    "lvs_ct_string_pin", "lvs_ctx_br_split", "lvs_ctx_set_br_split",
     "lvs_server_create", "lvs_server_submit", "lvs_server_poll", "lvs_server_stats_get", "lvs_server_free",
 ]
 
@@ -136,6 +136,8 @@ def _declare(L):
         "lvs_ctx_prepare_fft64": ([vp, vp], i32),
         "lvs_ctx_autotune": ([vp], i32),
         "lvs_ct_string_pin": ([vp], i32),
+        "lvs_ctx_br_split": ([vp, ctypes.POINTER(sz)], i32),
+        "lvs_ctx_set_br_split": ([vp, sz], i32),
         "lvs_preprocess_batch": ([vp, vpp, sz, ctypes.c_char_p, sz, vpp], i32),
         "lvs_probe_int_mul": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
         "lvs_ctx_ks_plan": ([vp, sz, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
@@ -530,6 +532,16 @@ def lvs_ctx_ks_plan(ctx, njobs):
     a, b = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().lvs_ctx_ks_plan(ctx, njobs, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def lvs_ctx_br_split(ctx):
+    v = ctypes.c_size_t()
+    _check(lib().lvs_ctx_br_split(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def lvs_ctx_set_br_split(ctx, max_jobs):
+    _check(lib().lvs_ctx_set_br_split(ctx, max_jobs))
 
 
 def lvs_ctx_set_ks_plan(ctx, njobs, jobs_per_cta, split):

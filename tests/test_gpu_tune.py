@@ -79,3 +79,55 @@ def test_int_mul_probe_plausible():
     lo, hi = L.lvs_probe_int_mul(0)
     assert 8 <= lo <= 128 and 4 <= hi <= 128
     assert hi <= lo * 1.05
+
+
+@pytest.mark.parametrize("which", ["test", "default"])
+def test_three_cta_blind_rotation_bit_exact(which):
+    """The blind rotation split over a cluster of three CTAs (one per NTT
+    prime) gives the same ciphertexts as one CTA per ciphertext and as the
+    oracle, for PBS launches and for the edit-distance pipeline (cell
+    epilogue, band taps)."""
+    params, oparams = (L.lvs_params_test(), T.params_test()) if which == "test" else \
+        (L.lvs_params_default(), T.params_lvs())
+    ck, sk = L.lvs_keygen(params, 4)
+    ctx = L.lvs_ctx_create(sk, 0)
+    K = T.Keys(oparams, 4)
+    big = K.big_dim
+    count = 40 if which == "test" else 9
+    rng = np.random.default_rng(11)
+    msgs = rng.integers(0, 32, size=count)
+    luts = rng.integers(0, 32, size=(count, 16), dtype=np.uint8)
+    cts = np.stack([T.encrypt(K, int(m), 13, 2, i) for i, m in enumerate(msgs)])
+    d_in = torch.from_numpy(cts.view(np.int64)).cuda()
+    d_lut = torch.from_numpy(luts).cuda()
+    outs = []
+    for split in (0, 10 ** 6):
+        L.lvs_ctx_set_br_split(ctx, split)
+        assert L.lvs_ctx_br_split(ctx) == split
+        d_out = torch.zeros_like(d_in)
+        L.lvs_pbs_batch_device(ctx, d_in, big + 1, d_lut, d_out, big + 1, count)
+        L.lvs_ctx_synchronize(ctx)
+        outs.append(d_out.cpu().numpy().view(np.uint64).copy())
+    assert np.array_equal(outs[0], outs[1])
+    if which == "test":
+        assert np.array_equal(outs[1], T.pbs_many(K, cts, luts.astype(np.uint32)))
+        # the pipeline: cell epilogue and band taps through the three-CTA form
+        pairs = [("kitten", "sittin"), ("abc", "abd")]
+        A = [L.lvs_encrypt_string(ck, a, L.LVS_ALPHA_ASCII7, 14, 2 * k) for k, (a, b) in enumerate(pairs)]
+        B = [L.lvs_encrypt_string(ck, b, L.LVS_ALPHA_ASCII7, 14, 2 * k + 1) for k, (a, b) in enumerate(pairs)]
+        for band in (-1, 2):
+            res = []
+            for split in (0, 10 ** 6):
+                L.lvs_ctx_set_br_split(ctx, split)
+                r = L.lvs_edit_distance_batch(ctx, A, B, L.lvs_opts_default(band=band))
+                res.append([L.lvs_result_export(r, k, big) for k in range(len(pairs))])
+                assert L.lvs_decrypt_all(ck, r) == [P.wf_distance(a, b) for a, b in pairs]
+            for x, y in zip(*res):
+                assert np.array_equal(x, y)
+    L.lvs_ctx_free(ctx)
+
+
+def test_autotune_sets_blind_rotation_split(full):
+    ck, ctx, K = full
+    L.lvs_ctx_autotune(ctx)
+    assert 0 <= L.lvs_ctx_br_split(ctx) <= 152
