@@ -411,7 +411,7 @@ lvs_status lvs_preprocess_batch(lvs_ctx *ctx, const lvs_ct_string *const *encs, 
         const size_t m = encs[k]->len, C = encs[k]->symbols, R = tabs[k]->subset.size();
         base[k] = rows;
         rows += m * C + (C == 2 ? R * m : 0);
-        if (R * m && cudaMalloc((void **)&tabs[k]->d, R * m * tabs[k]->stride * 8) != cudaSuccess) {
+        if (R * m != 0 && cudaMalloc((void **)&tabs[k]->d, R * m * tabs[k]->stride * 8) != cudaSuccess) {
             cudaGetLastError();
             free_all();
             return set_error(LVS_ERR_OOM, "lvs_preprocess: device allocation of the table failed");
