@@ -332,6 +332,15 @@ def run_lvs(args):
             L.lvs_ct_string_upload(ctx, s)
         step = lambda: L.lvs_edit_distance_batch(ctx, A_dev, B_dev)
 
+    # noise budget of the workload (Section 3.1.3): the largest key variance of
+    # any pair (PBS-output units) against the budget for a 2^-64 failure rate
+    nb = L.lvs_noise_budget(params, -64.0)
+    worst_key = max((L.lvs_noise_plan(len(a), len(b), -1, 0)[1] for a, b in pairs), default=0.0)
+    noise = {"budget_key_var": nb, "max_key_var": worst_key,
+             "log2_pfail_worst_key": L.lvs_noise_pfail(params, worst_key),
+             "refreshed": worst_key > nb,
+             "note": "key variance in PBS-output variances; refresh of dv/dh only above the budget"}
+
     # warm-up (+ correctness of every distance)
     r = None
     for w in range(max(1, args.warmup)):
@@ -495,6 +504,7 @@ def run_lvs(args):
                            "note": "batched: all pairs of a step complete together"},
             "one_pair_at_a_time": serial,
             "table_build": table_build,
+            "noise": noise,
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,

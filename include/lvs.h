@@ -195,6 +195,10 @@ void lvs_opts_default(lvs_opts *o);
  * of expected weight) decodes wrongly with probability at most 2^log2_pfail
  * (log2_pfail < 0).  Host only. */
 lvs_status lvs_noise_budget(const lvs_params *p, double log2_pfail, double *budget);
+/* log2 of the failure probability of one bootstrap whose key carries key_var
+ * PBS-output variances (plus the key-switch and modulus-switch noise): the
+ * normal tail beyond half a plaintext step.  Host only. */
+lvs_status lvs_noise_pfail(const lvs_params *p, double key_var, double *log2_pfail);
 /* Refresh plan of one m x n difference matrix (band < 0: full; else the
  * cells of lvs_opts.band).  Each M and EQ9 is a unit noise, dv_out = M - dh_in,
  * dh_out = M - dv_in; a cell costs the larger variance of its key and of its

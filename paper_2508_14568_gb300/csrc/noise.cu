@@ -146,20 +146,31 @@ lvs_status noise_plan(size_t m, size_t n, long band, double budget, std::vector<
     return LVS_OK;
 }
 
-double noise_budget(const lvs_params &p, double log2_pfail)
+namespace {
+struct BootstrapVariances {
+    double pbs, ks, ms;   // torus Z_2^64, binary keys of expected weight half their length
+};
+
+BootstrapVariances bootstrap_variances(const lvs_params &p)
 {
-    // variances on the torus Z_2^64, binary keys of expected weight half their length
+    BootstrapVariances v;
     const double big = (double)p.k * p.N;
     const int beta_pbs = (int)(p.pbs_level * p.pbs_base_log);
     const double r_pbs = std::ldexp(1.0, 2 * (63 - beta_pbs)) / 3.0;
-    const double var_pbs = (p.n / 2.0) * (1.0 + big / 2.0) * r_pbs +
-                           (double)p.n * (p.k + 1) * p.pbs_level * p.N * digit_sq(p.pbs_base_log) *
-                               tuniform_var(p.glwe_noise_log2);
+    v.pbs = (p.n / 2.0) * (1.0 + big / 2.0) * r_pbs +
+            (double)p.n * (p.k + 1) * p.pbs_level * p.N * digit_sq(p.pbs_base_log) * tuniform_var(p.glwe_noise_log2);
     const int beta_ks = (int)(p.ks_level * p.ks_base_log);
-    const double var_ks = (big / 2.0) * std::ldexp(1.0, 2 * (63 - beta_ks)) / 3.0 +
-                          big * p.ks_level * digit_sq(p.ks_base_log) * tuniform_var(p.lwe_noise_log2);
+    v.ks = (big / 2.0) * std::ldexp(1.0, 2 * (63 - beta_ks)) / 3.0 +
+           big * p.ks_level * digit_sq(p.ks_base_log) * tuniform_var(p.lwe_noise_log2);
     const double step = std::ldexp(1.0, 64) / (2.0 * p.N);
-    const double var_ms = (1.0 + p.n / 2.0) * step * step / 12.0;
+    v.ms = (1.0 + p.n / 2.0) * step * step / 12.0;
+    return v;
+}
+}  // namespace
+
+double noise_budget(const lvs_params &p, double log2_pfail)
+{
+    const BootstrapVariances v = bootstrap_variances(p);
     // z with erfc(z / sqrt 2) = 2^log2_pfail
     const double target = std::exp2(log2_pfail);
     double lo = 0, hi = 40;
@@ -169,8 +180,21 @@ double noise_budget(const lvs_params &p, double log2_pfail)
         else hi = mid;
     }
     const double z = 0.5 * (lo + hi);
-    const double room = std::pow(std::ldexp(1.0, 58) / z, 2) - var_ks - var_ms;
-    return room / var_pbs;
+    const double room = std::pow(std::ldexp(1.0, 58) / z, 2) - v.ks - v.ms;
+    return room / v.pbs;
+}
+
+// log2 of the probability that a key of key_var PBS-output variances (plus the
+// key-switch and modulus-switch noise) leaves the half-step 2^58: erfc(2^58 / (sigma sqrt 2))
+double noise_log2_pfail(const lvs_params &p, double key_var)
+{
+    const BootstrapVariances v = bootstrap_variances(p);
+    const double sigma = std::sqrt(key_var * v.pbs + v.ks + v.ms);
+    const double x = std::ldexp(1.0, 58) / (sigma * std::sqrt(2.0));
+    const double pf = std::erfc(x);
+    if (pf > 0) return std::log2(pf);
+    // erfc(x) ~ exp(-x^2) / (x sqrt(pi)) for large x
+    return (-x * x - std::log(x * std::sqrt(3.14159265358979323846))) / std::log(2.0);
 }
 
 lvs_status plan_refresh(const lvs_ctx *ctx, int32_t refresh_budget, PairRows &P)
@@ -201,6 +225,16 @@ lvs_status lvs_noise_budget(const lvs_params *p, double log2_pfail, double *budg
     if (st != LVS_OK) return st;
     if (!(log2_pfail < 0) || log2_pfail < -1000) return set_error(LVS_ERR_ARG, "lvs_noise_budget: log2_pfail out of range");
     *budget = noise_budget(*p, log2_pfail);
+    return LVS_OK;
+}
+
+lvs_status lvs_noise_pfail(const lvs_params *p, double key_var, double *log2_pfail)
+{
+    if (!p || !log2_pfail) return set_error(LVS_ERR_ARG, "lvs_noise_pfail: NULL argument");
+    lvs_status st = check_params(*p);
+    if (st != LVS_OK) return st;
+    if (!(key_var >= 0)) return set_error(LVS_ERR_ARG, "lvs_noise_pfail: negative variance");
+    *log2_pfail = noise_log2_pfail(*p, key_var);
     return LVS_OK;
 }
 

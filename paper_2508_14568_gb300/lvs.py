@@ -37,6 +37,7 @@ EXPORTS = [
     "lvs_ctx_prepare_fft64", "lvs_pbs_batch_device_fft64", "lvs_noise_budget", "lvs_noise_plan",
     "lvs_ctx_autotune", "lvs_ctx_ks_plan", "lvs_ctx_set_ks_plan", "lvs_probe_int_mul", "lvs_preprocess_batch",
     "lvs_ct_string_pin", "lvs_ctx_br_split", "lvs_ctx_set_br_split",
+    "lvs_noise_pfail",
     "lvs_server_create", "lvs_server_submit", "lvs_server_poll", "lvs_server_stats_get", "lvs_server_free",
 ]
 
@@ -143,6 +144,7 @@ def _declare(L):
         "lvs_ctx_ks_plan": ([vp, sz, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "lvs_ctx_set_ks_plan": ([vp, sz, i32, i32], i32),
         "lvs_noise_budget": ([ctypes.POINTER(lvs_params), ctypes.c_double, ctypes.POINTER(ctypes.c_double)], i32),
+        "lvs_noise_pfail": ([ctypes.POINTER(lvs_params), ctypes.c_double, ctypes.POINTER(ctypes.c_double)], i32),
         "lvs_noise_plan": ([sz, sz, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_uint8),
                             ctypes.POINTER(ctypes.c_double)], i32),
         "lvs_keyswitch_batch_device": ([vp, vp, sz, vp, sz], i32),
@@ -257,6 +259,12 @@ def lvs_noise_budget(params, log2_pfail=-64.0):
     b = ctypes.c_double()
     _check(lib().lvs_noise_budget(ctypes.byref(params), ctypes.c_double(log2_pfail), ctypes.byref(b)))
     return b.value
+
+
+def lvs_noise_pfail(params, key_var):
+    v = ctypes.c_double()
+    _check(lib().lvs_noise_pfail(ctypes.byref(params), ctypes.c_double(key_var), ctypes.byref(v)))
+    return v.value
 
 
 def lvs_noise_plan(m, n, band, budget):

@@ -113,3 +113,20 @@ def test_budget_too_small_is_an_error(small):
     with pytest.raises(L.LvsError) as ei:
         _run(ck, ctx, [("abcdefgh", "hgfedcba")], P.ALPHA_ASCII7, 65, 10)
     assert ei.value.status == L.LVS_ERR_NOISE_BUDGET
+
+
+def test_refresh_full_parameters_long_pair():
+    """Refresh at the full parameter set on a longer DNA pair with a small
+    budget: exact distance, one extra PBS per refreshed cell."""
+    ck, sk = L.lvs_keygen(L.lvs_params_default(), 2)
+    ctx = L.lvs_ctx_create(sk, 0)
+    rng = random.Random(8)
+    a = "".join(rng.choice(W.DNA) for _ in range(40))
+    b = W.mutate_rate(rng, a, W.DNA, 0.15)
+    pairs = [(a, b)]
+    r, d, npbs = _run(ck, ctx, pairs, P.ALPHA_DNA4, 66, 30)
+    diags, worst = Nz.refresh_schedule(len(a), len(b), None, 30)
+    assert worst <= 30 and len(diags) > 5
+    assert d == [P.wf_distance(a, b)]
+    assert npbs == 2 * len(a) * len(b) + _refreshed_cells(len(a), len(b), set(diags))
+    L.lvs_ctx_free(ctx)

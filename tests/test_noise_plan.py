@@ -43,3 +43,14 @@ def test_budget_matches_oracle(which):
     # 256 characters need no refresh at the default parameters
     assert 14 * 255 + 10 < L.lvs_noise_budget(L.lvs_params_default(), -64.0)
     assert math.isfinite(L.lvs_noise_budget(p, -64.0))
+
+
+@pytest.mark.parametrize("which", ["default", "test"])
+def test_pfail_matches_oracle(which):
+    p = L.lvs_params_default() if which == "default" else L.lvs_params_test()
+    op = (T.params_lvs() if which == "default" else T.params_test()).as_dict()
+    for kv in (1.0, 3580.0, 1e5, 1e6, 9e6):
+        want = math.log2(max(Nz.pfail_of(op, kv), 1e-300))
+        assert abs(L.lvs_noise_pfail(p, kv) - want) < 1e-6
+    # at the budget for 2^-64 the failure probability is 2^-64
+    assert abs(L.lvs_noise_pfail(p, L.lvs_noise_budget(p, -64.0)) + 64) < 1e-6
