@@ -146,6 +146,20 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
+# ----------------------------------------------------------------------------- checks
+
+def levenshtein(a, b):
+    """Plain edit distance (two-row Wagner-Fischer), to check every decrypted
+    distance the bench produces."""
+    prev = list(range(len(b) + 1))
+    for i, ca in enumerate(a, 1):
+        cur = [i] + [0] * len(b)
+        for j, cb in enumerate(b, 1):
+            cur[j] = min(prev[j] + 1, cur[j - 1] + 1, prev[j - 1] + (ca != cb))
+        prev = cur
+    return prev[-1]
+
+
 # ----------------------------------------------------------------------------- oracle timing
 
 def oracle_sample(pairs, alpha, count, seed=0):
@@ -271,7 +285,6 @@ class Ranks:
 def run_lvs(args):
     import torch
     import torch.distributed as dist
-    from oracle import plain as P  # WF for the distance check only (plaintext)
     from paper_2508_14568_gb300 import lvs as L
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -301,7 +314,7 @@ def run_lvs(args):
     br_split = L.lvs_ctx_br_split(ctx)
     big = params.k * params.N
     cells = sum(len(a) * len(b) for a, b in pairs)
-    want = [P.wf_distance(a, b) for a, b in pairs]
+    want = [levenshtein(a, b) for a, b in pairs]
 
     def encrypt_all(seed):
         if cfg == 3:
@@ -520,7 +533,6 @@ def run_serving(args):
     U[4,64]) against plaintext or encrypted references (U[4,64], 50/50) into the
     continuous-batching server; latency = completion - arrival."""
     import torch
-    from oracle import plain as P
     from paper_2508_14568_gb300 import lvs as L
     from paper_2508_14568_gb300 import workloads as W
     arrivals = W.config5(rate=args.rate, duration=args.duration)
@@ -559,7 +571,7 @@ def run_serving(args):
     clk = clocks.stop()
     st = L.lvs_server_stats_get(server)
     lat = sorted(done_t[i] - submit_t[i] for i in done_t)
-    ok = all(L.lvs_decrypt(ck, results[i], 0) == P.wf_distance(arrivals[i][1], arrivals[i][2]) for i in results)
+    ok = all(L.lvs_decrypt(ck, results[i], 0) == levenshtein(arrivals[i][1], arrivals[i][2]) for i in results)
     cells = sum(len(q) * len(ref) for _, q, ref, _ in arrivals)
     line = {"metric": "serving p50/p99 query latency", "config": {
                 "workload": "config 5: Poisson %.1f queries/s for %.0f s, 27 symbols, lengths U[4,64], "
