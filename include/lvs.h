@@ -292,6 +292,8 @@ typedef struct lvs_server_stats {
     uint64_t max_step_pbs;      /* widest launch step                            */
     uint64_t mem_in_use;        /* device bytes held by admitted queries         */
     double busy_ms;             /* wall time spent inside launch steps           */
+    uint64_t requeued;          /* admissions retried after a failed device      *
+                                 * allocation while other queries held memory    */
 } lvs_server_stats;
 
 /* Continuous batching (Section 6.2 parallelism across cells and across
@@ -303,6 +305,9 @@ typedef struct lvs_server_stats {
  * mem_budget_bytes (one query is always admitted when none runs).  The
  * context must not be used by other threads while the server exists. */
 lvs_status lvs_server_create(lvs_ctx *ctx, size_t mem_budget_bytes, size_t max_active, lvs_server **out);
+/* A query whose device allocation fails at admission goes back to the head
+ * of the queue while other queries run (their memory frees up as they
+ * finish); alone, it completes with LVS_ERR_OOM. */
 /* Copies the query (the caller may free its strings afterwards) and returns a
  * ticket.  LVS_ERR_ARG if a symbol is outside the alphabet or the query alone
  * exceeds the budget. */
@@ -394,6 +399,13 @@ lvs_status lvs_ctx_set_ks_plan(lvs_ctx *ctx, size_t njobs, int32_t jobs_per_cta,
  * off; LVS_ERR_STATE if the device cannot run it. */
 lvs_status lvs_ctx_br_split(lvs_ctx *ctx, size_t *max_jobs);
 lvs_status lvs_ctx_set_br_split(lvs_ctx *ctx, size_t max_jobs);
+
+/* Test hook (host-side fault injection, no counterpart in the paper): the
+ * next `count` allocations of batch / query device memory fail as if the
+ * device were out of memory (LVS_ERR_OOM), without allocating.  0 clears it.
+ * Lets the error paths (batch calls, server admission) be tested without
+ * exhausting or faulting a GPU. */
+void lvs_debug_fail_allocations(int32_t count);
 
 /* Measured issue rate of 32-bit integer multiplies on `device`: low-half
  * (mul.lo / IMAD) and high-half (mul.hi) results per SM per clock, from one

@@ -16,17 +16,32 @@
 // It is allocated stream-ordered and released when the batch has been copied
 // into its result.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "lvs_internal.hpp"
 
 namespace lvs {
 
+// host-side fault injection (lvs_debug_fail_allocations)
+static std::atomic<int> g_fail_allocs{0};
+
+static bool injected_failure()
+{
+    int c = g_fail_allocs.load();
+    while (c > 0)
+        if (g_fail_allocs.compare_exchange_weak(c, c - 1)) return true;
+    return false;
+}
+
 lvs_status arena_alloc(lvs_ctx *ctx, size_t rows, Arena &A)
 {
     A.stride = (size_t)ctx->P.big() + 2;
     A.rows = rows;
+    A.d = nullptr;
     if (rows == 0) return LVS_OK;
+    if (injected_failure())
+        return set_error(LVS_ERR_OOM, "device allocation of the batch arena failed (injected)");
     if (cudaMallocAsync((void **)&A.d, rows * A.stride * 8, ctx->stream) != cudaSuccess) {
         cudaGetLastError();
         return set_error(LVS_ERR_OOM, "device allocation of the batch arena failed (" +
@@ -224,6 +239,8 @@ lvs_status check_ctx_string(const lvs_ctx *ctx, const lvs_ct_string *s)
 using namespace lvs;
 
 extern "C" {
+
+void lvs_debug_fail_allocations(int32_t count) { g_fail_allocs.store(count > 0 ? count : 0); }
 
 lvs_status lvs_edit_distance_batch(lvs_ctx *ctx, const lvs_ct_string *const *a, const lvs_ct_string *const *b,
                                    size_t npairs, const lvs_opts *opts, lvs_result **out)

@@ -202,14 +202,34 @@ void worker_loop(lvs_server *S)
             }
             S->stats.pending = S->pending.size();
         }
+        std::vector<Query *> retry;
         for (Query *q : admitted) {
             lvs_status st;
             {
                 std::lock_guard<std::mutex> lk(ctx->mu);
                 st = setup(ctx, *q);
             }
+            if (st == LVS_ERR_OOM && !S->active.empty()) {
+                // memory is held by running queries: try again at a later step
+                {
+                    std::lock_guard<std::mutex> lk(ctx->mu);
+                    arena_free(ctx, q->A);
+                }
+                retry.push_back(q);
+                continue;
+            }
             if (st != LVS_OK) { complete(S, q, st, lvs_last_error(), nullptr); continue; }
             S->active.push_back(q);
+        }
+        if (!retry.empty()) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (auto it = retry.rbegin(); it != retry.rend(); ++it) {
+                S->used -= (*it)->bytes;
+                S->pending.push_front(*it);
+                S->stats.admitted -= 1;
+                S->stats.requeued += 1;
+            }
+            S->stats.pending = S->pending.size();
         }
         jobs.clear();
         for (Query *q : S->active) plan_query(*q, jobs);

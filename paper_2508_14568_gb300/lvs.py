@@ -37,7 +37,7 @@ EXPORTS = [
     "lvs_ctx_prepare_fft64", "lvs_pbs_batch_device_fft64", "lvs_noise_budget", "lvs_noise_plan",
     "lvs_ctx_autotune", "lvs_ctx_ks_plan", "lvs_ctx_set_ks_plan", "lvs_probe_int_mul", "lvs_preprocess_batch",
     "lvs_ct_string_pin", "lvs_ctx_br_split", "lvs_ctx_set_br_split",
-    "lvs_noise_pfail",
+    "lvs_noise_pfail", "lvs_debug_fail_allocations",
     "lvs_server_create", "lvs_server_submit", "lvs_server_poll", "lvs_server_stats_get", "lvs_server_free",
 ]
 
@@ -69,7 +69,8 @@ class lvs_query(ctypes.Structure):
 
 class lvs_server_stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "admitted", "completed", "pending", "active", "steps",
-                                               "pbs", "max_step_pbs", "mem_in_use")] + [("busy_ms", ctypes.c_double)]
+                                               "pbs", "max_step_pbs", "mem_in_use")] + [("busy_ms", ctypes.c_double),
+                                                                                        ("requeued", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -137,6 +138,7 @@ def _declare(L):
         "lvs_ctx_prepare_fft64": ([vp, vp], i32),
         "lvs_ctx_autotune": ([vp], i32),
         "lvs_ct_string_pin": ([vp], i32),
+        "lvs_debug_fail_allocations": ([i32], None),
         "lvs_ctx_br_split": ([vp, ctypes.POINTER(sz)], i32),
         "lvs_ctx_set_br_split": ([vp, sz], i32),
         "lvs_preprocess_batch": ([vp, vpp, sz, ctypes.c_char_p, sz, vpp], i32),
@@ -259,6 +261,10 @@ def lvs_noise_budget(params, log2_pfail=-64.0):
     b = ctypes.c_double()
     _check(lib().lvs_noise_budget(ctypes.byref(params), ctypes.c_double(log2_pfail), ctypes.byref(b)))
     return b.value
+
+
+def lvs_debug_fail_allocations(count):
+    lib().lvs_debug_fail_allocations(count)
 
 
 def lvs_noise_pfail(params, key_var):
@@ -510,6 +516,11 @@ def lvs_server_poll(server, ticket):
         return None
     _check(st)
     return Result(out.value)
+
+
+def lvs_server_free(server):
+    """Stops the server's worker and frees it now (otherwise when the handle is collected)."""
+    server.__del__()
 
 
 def lvs_server_stats_get(server):

@@ -127,3 +127,56 @@ def test_server_merges_arrivals_while_running(setup):
     assert [L.lvs_decrypt(ck, r, 0) for r in res] == [P.wf_distance(a, b) for a, b, _ in qs]
     st = L.lvs_server_stats_get(server)
     assert st["steps"] >= 1 and st["pbs"] > 0
+
+
+def test_batch_call_reports_injected_allocation_failure(setup):
+    """Host-side fault injection: a failed device allocation is an error
+    status (LVS_ERR_OOM), not a crash, and the next call works."""
+    ck, ctx, _ = setup
+    A = [L.lvs_encrypt_string(ck, "ABC", L.LVS_ALPHA_27, 91, 0)]
+    B = [L.lvs_encrypt_string(ck, "ABD", L.LVS_ALPHA_27, 91, 1)]
+    L.lvs_debug_fail_allocations(1)
+    with pytest.raises(L.LvsError) as ei:
+        L.lvs_edit_distance_batch(ctx, A, B)
+    assert ei.value.status == L.LVS_ERR_OOM
+    r = L.lvs_edit_distance_batch(ctx, A, B)
+    assert L.lvs_decrypt_all(ck, r) == [1]
+
+
+def test_server_requeues_a_query_whose_allocation_failed(setup):
+    ck, ctx, _ = setup
+    server = L.lvs_server_create(ctx, 1 << 34)
+    import random
+    rng = random.Random(92)
+    long_a = "".join(rng.choice(W.ALPHA27[:5]) for _ in range(120))
+    long_b = "".join(rng.choice(W.ALPHA27[:5]) for _ in range(120))
+    qs = [(long_a, long_b, False), ("HELLO", "HALLO", True)]
+    t1 = _submit(ck, server, qs[:1], 93)
+    t0 = time.time()
+    while L.lvs_server_stats_get(server)["active"] < 1:
+        assert time.time() - t0 < 30
+        time.sleep(0.0005)
+    L.lvs_debug_fail_allocations(1)      # the next admission's allocation fails
+    t2 = _submit(ck, server, qs[1:], 94)
+    res = _collect(server, t1 + t2)
+    st = L.lvs_server_stats_get(server)
+    L.lvs_debug_fail_allocations(0)
+    assert st["requeued"] >= 1
+    for r, (a, b, _) in zip(res, qs):
+        assert L.lvs_decrypt(ck, r, 0) == P.wf_distance(a, b)
+    L.lvs_server_free(server)
+
+
+def test_server_lone_query_allocation_failure_is_reported(setup):
+    ck, ctx, _ = setup
+    server = L.lvs_server_create(ctx, 1 << 34)
+    L.lvs_debug_fail_allocations(1)
+    t = _submit(ck, server, [("AB", "BA", True)], 95)
+    t0 = time.time()
+    with pytest.raises(L.LvsError) as ei:
+        while L.lvs_server_poll(server, t[0]) is None:
+            assert time.time() - t0 < 30
+            time.sleep(0.002)
+    assert ei.value.status == L.LVS_ERR_OOM
+    L.lvs_debug_fail_allocations(0)
+    L.lvs_server_free(server)
