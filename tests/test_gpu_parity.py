@@ -340,3 +340,15 @@ def test_config2_full_size_distances(full):
     pairs = W.config2()
     r, d = _gpu_batch(full, pairs, P.ALPHA_ASCII7, seed=0)
     assert d == [P.wf_distance(a, b) for a, b in pairs]
+
+
+def test_long_pairs_deep_wavefront(small):
+    """Long strings: thousands of anti-diagonal steps, wide launches and large
+    arenas (test parameters keep it fast); every distance equals WF."""
+    S = small
+    import random
+    rng = random.Random(77)
+    a = "".join(rng.choice(W.DNA) for _ in range(700))
+    pairs = [(a, W.mutate_rate(rng, a, W.DNA, 0.2)), (a[:300], a[:650]), ("A" * 500, "C" * 20)]
+    r, d = _gpu_batch(S, pairs, P.ALPHA_DNA4, seed=78)
+    assert d == [P.wf_distance(x, y) for x, y in pairs]
