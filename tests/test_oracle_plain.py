@@ -292,3 +292,18 @@ def test_non_square_band_exact_and_upper_bound():
         assert d >= wf
         if wf <= abs(n - m) + 2 * band:
             assert d == wf
+
+
+def test_table_tab_pbs_band_rows():
+    """Table tab_pbs: Exact Skipping ~ 2.25 m n and Approx. l = 10 ~ 60 n
+    follow from the band count of Section 3.2 with 3 PBS per cell (the printed
+    approximations drop the corner terms; l = m/4 is ~ 6 l n minus 3 l^2)."""
+    m = 256
+    skip = 3 * P.band_cells(m, m // 2)
+    assert abs(skip / (m * m) - 2.25) < 0.01
+    approx10 = 3 * P.band_cells(m, 10)
+    assert abs(approx10 / (60 * m) - 1) < 0.05
+    l = m // 4
+    approx_q = 3 * P.band_cells(m, l)
+    assert approx_q == 6 * l * m + 3 * m - 3 * l * l - 3 * l
+    assert abs(approx_q / (6 * l * m) - 1) < 0.15
