@@ -58,8 +58,9 @@ typedef enum { LVS_ALPHA_ASCII7 = 0, LVS_ALPHA_27 = 1, LVS_ALPHA_DNA4 = 2 } lvs_
 
 /* TFHE parameters (Section 2.2 and Section 6.2 name only the family "4-bit
  * message, 0-bit carry" with a padding bit; numeric values are chosen by this
- * library).  Supported: k = 1, N in {512, 2048}, pbs_level * pbs_base_log <= 26
- * with pbs_level in {1, 2}, ks_level * ks_base_log <= 30. */
+ * library).  Supported: k = 1, N in {512, 2048}, pbs_level = 2 with
+ * pbs_level * pbs_base_log <= 26, ks_level <= 8 with ks_level * ks_base_log
+ * <= 30, 1 <= n <= 4096; LVS_ERR_ARG otherwise. */
 typedef struct lvs_params {
     uint32_t n;               /* LWE dimension after key switching           */
     uint32_t k;               /* GLWE dimension (1)                          */
@@ -259,8 +260,9 @@ lvs_status lvs_edit_distance_preprocessed_batch(lvs_ctx *ctx, const lvs_eq_table
 
 /* Number of items in a result, and for item `pair`: m and n. */
 lvs_status lvs_result_info(const lvs_result *r, size_t *items, size_t pair, size_t *m, size_t *n);
-/* Copies the ciphertexts of item `pair` (n big LWE ciphertexts, or 1 for
- * lvs_eq) to host memory dst ([n][k*N+1]).  dst = NULL: size query. */
+/* Copies the ciphertexts of item `pair` (n big LWE ciphertexts; m + n with a
+ * band; 1 for lvs_eq) to host memory dst ([rows][k*N+1]).  dst = NULL: size
+ * query in *words. */
 lvs_status lvs_result_export(const lvs_result *r, size_t pair, uint64_t *dst, size_t *words);
 void lvs_result_free(lvs_result *r);
 
@@ -302,12 +304,12 @@ typedef struct lvs_server_stats {
  * work of every admitted query; queries are admitted in arrival order while
  * a slot is free (at most max_active admitted queries; 0 = no slot limit) and
  * their device footprint (ciphertext state, frontier, tables, result) fits
- * mem_budget_bytes (one query is always admitted when none runs).  The
- * context must not be used by other threads while the server exists. */
+ * mem_budget_bytes (one query is always admitted when none runs).  A query
+ * whose device allocation fails at admission goes back to the head of the
+ * queue while other queries run (their memory frees up as they finish);
+ * alone, it completes with LVS_ERR_OOM.  The context must not be used by
+ * other threads while the server exists. */
 lvs_status lvs_server_create(lvs_ctx *ctx, size_t mem_budget_bytes, size_t max_active, lvs_server **out);
-/* A query whose device allocation fails at admission goes back to the head
- * of the queue while other queries run (their memory frees up as they
- * finish); alone, it completes with LVS_ERR_OOM. */
 /* Copies the query (the caller may free its strings afterwards) and returns a
  * ticket.  LVS_ERR_ARG if a symbol is outside the alphabet or the query alone
  * exceeds the budget. */
@@ -364,9 +366,9 @@ lvs_status lvs_pbs_batch_device_fft64(lvs_ctx *ctx, const uint64_t *d_in, size_t
  * LVS_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the
  * process exits.  Limit: count * (64 + 4 (n+1)) bytes plus up to 255 bytes of
  * alignment must fit, i.e. at most 1232 PBS per call for n = 834 (12944 for
- * n = 64); larger counts fail with LVS_ERR_ARG and do nothing.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the one array and every call rewrites
+ * n = 64); larger counts fail with LVS_ERR_ARG and do nothing.  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share the one array and every call rewrites
  * the part it uses before reading it (nothing needs to start at zero): calls
  * that overlap on the GPU -- different streams or contexts of the same device
  * -- race on it; issue them on one stream or serialise them. */
