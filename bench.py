@@ -312,6 +312,7 @@ def run_lvs(args):
     L.lvs_ctx_autotune(ctx)
     ks_plans = {str(nj): list(L.lvs_ctx_ks_plan(ctx, nj)) for nj in (4, 16, 64, 256, 1024, 4096)}
     br_split = L.lvs_ctx_br_split(ctx)
+    ks_gemm_min = L.lvs_ctx_ks_gemm_min(ctx)
     big = params.k * params.N
     cells = sum(len(a) * len(b) for a, b in pairs)
     want = [levenshtein(a, b) for a, b in pairs]
@@ -512,7 +513,8 @@ def run_lvs(args):
             "kernels": {"blind_rotate": br, "keyswitch": ks,
                         "ks_plans": {"note": "launch size bucket end -> [PBS per CTA, split] (lvs_ctx_autotune)",
                                      "plans": ks_plans},
-                        "br_three_cta_max_pbs": br_split},
+                        "br_three_cta_max_pbs": br_split,
+                        "ks_tensor_core_min_pbs": ks_gemm_min},
             "latency_ms": {"p50": batched_latency_ms, "p99": batched_latency_ms,
                            "note": "batched: all pairs of a step complete together"},
             "one_pair_at_a_time": serial,

@@ -383,7 +383,8 @@ lvs_status lvs_pbs_batch_device_noalloc(lvs_ctx *ctx, const uint64_t *d_in, size
  * the 2048 input coefficients split over 1..32 CTAs with a finishing
  * reduction -- on synthetic jobs and keeps the fastest in the context; for
  * the blind rotation it finds the largest launch size for which the
- * three-CTA form (lvs_ctx_set_br_split) is faster.
+ * three-CTA form (lvs_ctx_set_br_split) is faster, and for the key switch the
+ * launch size from which the tensor-core form (lvs_ctx_set_ks_gemm_min) is.
  * Without it a heuristic plan is used (fill about two CTAs per SM).  Every
  * plan gives the same result bit for bit.  Synchronous; takes about a second;
  * allocates and frees its own scratch. */
@@ -401,6 +402,15 @@ lvs_status lvs_ctx_set_ks_plan(lvs_ctx *ctx, size_t njobs, int32_t jobs_per_cta,
  * off; LVS_ERR_STATE if the device cannot run it. */
 lvs_status lvs_ctx_br_split(lvs_ctx *ctx, size_t *max_jobs);
 lvs_status lvs_ctx_set_br_split(lvs_ctx *ctx, size_t max_jobs);
+/* Key-switch launches of at least min_jobs PBS run as a dense product on the
+ * tensor cores: digits (|d| <= 4) times the key-switching key split into its
+ * eight bytes, bf16 x bf16 -> fp32 cuBLAS GEMMs over four chunks of the
+ * reduction dimension (every partial sum an integer below 2^22, so exact),
+ * recombined mod 2^64 -- the same result bit for bit.  Default 1024;
+ * lvs_ctx_autotune measures the crossover; 0 turns it off.  LVS_ERR_STATE if
+ * the context could not set it up (it then uses the kernel for every size). */
+lvs_status lvs_ctx_ks_gemm_min(lvs_ctx *ctx, size_t *min_jobs);
+lvs_status lvs_ctx_set_ks_gemm_min(lvs_ctx *ctx, size_t min_jobs);
 
 /* Test hook (host-side fault injection, no counterpart in the paper): the
  * next `count` allocations of batch / query device memory fail as if the

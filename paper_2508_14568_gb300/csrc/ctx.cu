@@ -129,7 +129,7 @@ static lvs_status launch_step(lvs_ctx *ctx, const Job *d_jobs, size_t nj, bool t
         LVS_CUDA(cudaEventRecord(a, ctx->stream));
     }
     int nks = 0;
-    LVS_CUDA(launch_keyswitch(ctx, d_jobs, nj, ctx->ms, ctx->stream, &nks));
+    LVS_CUDA(launch_keyswitch_auto(ctx, d_jobs, nj, ctx->ms, ctx->stream, &nks));
     if (timed) LVS_CUDA(cudaEventRecord(b, ctx->stream));
     LVS_CUDA(launch_blind_rotate(ctx, d_jobs, nj, ctx->ms, ctx->luts, 0, ctx->stream));
     if (timed) {
@@ -162,8 +162,11 @@ lvs_status run_steps(lvs_ctx *ctx, const std::vector<Job> &jobs, const std::vect
     LVS_CUDA(cudaMemcpyAsync(ctx->jobs, jobs.data(), jobs.size() * sizeof(Job), cudaMemcpyHostToDevice,
                              ctx->stream));
     const bool timed = ctx->timing.enabled;
+    // the tensor-core key switch goes through cuBLAS, which is not captured:
+    // runs with such a step launch directly
+    const bool gemm_step = ctx->ks_gemm && ctx->ks_gemm_min && widest >= ctx->ks_gemm_min;
     // graphs need a capturable stream (not the legacy default stream)
-    if (use_graph && !timed && ctx->stream != nullptr && off.size() > 2) {
+    if (use_graph && !timed && !gemm_step && ctx->stream != nullptr && off.size() > 2) {
         cudaGraph_t graph = nullptr;
         LVS_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
         lvs_status lst = LVS_OK;
@@ -254,6 +257,12 @@ lvs_status lvs_ctx_create(const lvs_server_key *sk, int device, void *stream, lv
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->ksk, sk->ksk.data(), sk->ksk.size() * 8, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = launch_ksk_colsum(ctx, ctx->stream);
+    if (e == cudaSuccess) {
+        // tensor-core key switch for large launches (optional: without it the
+        // kernel path serves every launch size)
+        if (ks_gemm_init(ctx) == LVS_OK && ctx->ks_gemm) ctx->ks_gemm_min = 1024;
+        else cudaGetLastError();
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(coef, sk->bsk.data(), sk->bsk.size() * 8, cudaMemcpyHostToDevice, ctx->stream);
     uint32_t mont[3][2];
@@ -277,6 +286,7 @@ void lvs_ctx_free(lvs_ctx *ctx)
     cudaFree(ctx->bsk_ntt);
     cudaFree(ctx->ksk);
     cudaFree(ctx->ksk_colsum);
+    ks_gemm_free(ctx);
     cudaFree(ctx->tw);
     cudaFree(ctx->luts);
     cudaFree(ctx->bsk_fft);
@@ -366,7 +376,7 @@ lvs_status lvs_pbs_batch_device(lvs_ctx *ctx, const uint64_t *d_in, size_t in_st
             LVS_CUDA(cudaEventRecord(a, ctx->stream));
         }
         int nks = 0;
-        LVS_CUDA(launch_keyswitch(ctx, ctx->jobs, nc, ctx->ms, ctx->stream, &nks));
+        LVS_CUDA(launch_keyswitch_auto(ctx, ctx->jobs, nc, ctx->ms, ctx->stream, &nks));
         if (timed) LVS_CUDA(cudaEventRecord(b, ctx->stream));
         LVS_CUDA(launch_blind_rotate(ctx, ctx->jobs, nc, ctx->ms, d_lut + c0 * 16, 1, ctx->stream));
         if (timed) {
@@ -396,7 +406,7 @@ lvs_status lvs_keyswitch_batch_device(lvs_ctx *ctx, const uint64_t *d_in, size_t
     if (st != LVS_OK) return st;
     LVS_CUDA(cudaMemcpyAsync(ctx->jobs, jobs.data(), count * sizeof(Job), cudaMemcpyHostToDevice, ctx->stream));
     int nks = 0;
-    LVS_CUDA(launch_keyswitch(ctx, ctx->jobs, count, d_out, ctx->stream, &nks));
+    LVS_CUDA(launch_keyswitch_auto(ctx, ctx->jobs, count, d_out, ctx->stream, &nks));
     ctx->launches += nks;
     return LVS_OK;
 }

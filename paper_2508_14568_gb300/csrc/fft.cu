@@ -339,7 +339,7 @@ lvs_status lvs_pbs_batch_device_fft64(lvs_ctx *ctx, const uint64_t *d_in, size_t
         if (st != LVS_OK) return st;
         LVS_CUDA(cudaMemcpyAsync(ctx->jobs, jobs.data(), nc * sizeof(Job), cudaMemcpyHostToDevice, ctx->stream));
         int nks = 0;
-        LVS_CUDA(launch_keyswitch(ctx, ctx->jobs, nc, ctx->ms, ctx->stream, &nks));
+        LVS_CUDA(launch_keyswitch_auto(ctx, ctx->jobs, nc, ctx->ms, ctx->stream, &nks));
         const unsigned grid = (unsigned)std::min<size_t>(nc, (size_t)ctx->fft_grid);
         if (p.N == 2048)
             fft::k_blind_rotate_fft<11><<<grid, fft::kThreads, fft::FftSmem<11>::total, ctx->stream>>>(

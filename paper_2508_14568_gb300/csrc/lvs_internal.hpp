@@ -118,6 +118,7 @@ struct Timing {
 }  // namespace lvs
 
 namespace lvs {
+struct KsGemm;   // tensor-core key switch (ks_gemm.cu)
 // key-switch launch shape: jobs per CTA (4 or 16) and split of the input
 // coefficients over gridDim.z; one plan per launch-size bucket
 struct KsPlan { int tj = 0; int split = 1; };
@@ -157,6 +158,8 @@ struct lvs_ctx {
     uint64_t *ks_part = nullptr;   // split key-switch partial sums
     size_t ks_part_cap = 0;        // words
     lvs::KsPlan ks_tuned[lvs::kKsBuckets];   // autotuned plans (tj = 0: default heuristic)
+    lvs::KsGemm *ks_gemm = nullptr;  // key switch as bf16 GEMMs (null: unavailable)
+    size_t ks_gemm_min = 0;          // launches of at least this many PBS use it (0: never)
     uint64_t pbs_done = 0;
     uint64_t launches = 0;
     lvs::Timing timing;
@@ -201,6 +204,14 @@ cudaError_t launch_keyswitch(const lvs_ctx *ctx, const Job *jobs, size_t njobs, 
                              int *nlaunch = nullptr);
 cudaError_t launch_keyswitch_plan(const lvs_ctx *ctx, const Job *jobs, size_t njobs, uint32_t *ms, uint64_t *part,
                                   KsPlan pl, cudaStream_t s);
+// tensor-core key switch (ks_gemm.cu)
+lvs_status ks_gemm_init(lvs_ctx *ctx);
+void ks_gemm_free(lvs_ctx *ctx);
+cudaError_t launch_keyswitch_gemm(const lvs_ctx *ctx, const Job *jobs, size_t njobs, uint32_t *ms, cudaStream_t s,
+                                  int *nlaunch);
+// the key switch of a launch, in the form its size calls for
+cudaError_t launch_keyswitch_auto(const lvs_ctx *ctx, const Job *jobs, size_t njobs, uint32_t *ms, cudaStream_t s,
+                                  int *nlaunch = nullptr);
 KsPlan ks_plan(const lvs_ctx *ctx, size_t njobs);
 size_t ks_part_words(const lvs_ctx *ctx, size_t njobs);
 cudaError_t launch_ksk_colsum(const lvs_ctx *ctx, cudaStream_t s);

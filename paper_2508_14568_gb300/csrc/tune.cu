@@ -1,5 +1,6 @@
 // Autotuner of the launch shapes: the key switch's (jobs per CTA and split
-// of the input coefficients over CTAs, per launch-size bucket) and the blind
+// of the input coefficients over CTAs, per launch-size bucket, and from which
+// launch size the tensor-core GEMM form takes over) and the blind
 // rotation's (one CTA per ciphertext, or three -- one per prime -- for small
 // launches).
 //
@@ -90,6 +91,7 @@ lvs_status lvs_ctx_autotune(lvs_ctx *ctx)
         return cuda_error(e, "lvs_ctx_autotune: set-up");
     }
     const int splits[] = {1, 2, 4, 8, 16, 32};
+    size_t gemm_min = 0;
     for (int b = 0; b < kKsBuckets && st == LVS_OK; ++b) {
         const size_t nj = kBucketSize[b];
         KsPlan best;
@@ -109,7 +111,25 @@ lvs_status lvs_ctx_autotune(lvs_ctx *ctx)
             if (st != LVS_OK) break;
         }
         if (st == LVS_OK) ctx->ks_tuned[b] = best;
+        // the tensor-core key switch against the best kernel plan of the
+        // bucket: the GEMM path serves every launch from the smallest
+        // bucket size where it is faster
+        if (st == LVS_OK && ctx->ks_gemm && nj >= 256) {
+            float tg = 1e30f;
+            for (int rep = 0; rep < 4 && st == LVS_OK; ++rep) {
+                cudaError_t e3 = cudaEventRecord(e0, ctx->stream);
+                if (e3 == cudaSuccess) e3 = launch_keyswitch_gemm(ctx, djobs, nj, ms, ctx->stream, nullptr);
+                if (e3 == cudaSuccess) e3 = cudaEventRecord(e1, ctx->stream);
+                if (e3 == cudaSuccess) e3 = cudaEventSynchronize(e1);
+                float ms_ = 0;
+                if (e3 == cudaSuccess) e3 = cudaEventElapsedTime(&ms_, e0, e1);
+                if (e3 != cudaSuccess) st = cuda_error(e3, "lvs_ctx_autotune: key-switch GEMM timing");
+                else if (rep > 0) tg = std::min(tg, ms_);
+            }
+            if (st == LVS_OK && tg < best_t && gemm_min == 0) gemm_min = nj;
+        }
     }
+    if (st == LVS_OK && ctx->ks_gemm) ctx->ks_gemm_min = gemm_min;
     // blind rotation: one CTA per ciphertext vs three CTAs (one per prime) per
     // ciphertext, on synthetic jobs (rotation amounts from a byte pattern);
     // the three-CTA form is kept up to the largest tested launch size where it
@@ -171,6 +191,22 @@ lvs_status lvs_ctx_ks_plan(lvs_ctx *ctx, size_t njobs, int32_t *jobs_per_cta, in
     const KsPlan pl = ks_plan(ctx, njobs);
     *jobs_per_cta = pl.tj;
     *split = pl.split;
+    return LVS_OK;
+}
+
+lvs_status lvs_ctx_ks_gemm_min(lvs_ctx *ctx, size_t *min_jobs)
+{
+    if (!ctx || !min_jobs) return set_error(LVS_ERR_ARG, "lvs_ctx_ks_gemm_min: NULL argument");
+    *min_jobs = ctx->ks_gemm ? ctx->ks_gemm_min : 0;
+    return LVS_OK;
+}
+
+lvs_status lvs_ctx_set_ks_gemm_min(lvs_ctx *ctx, size_t min_jobs)
+{
+    if (!ctx) return set_error(LVS_ERR_ARG, "lvs_ctx_set_ks_gemm_min: NULL context");
+    if (min_jobs > 0 && !ctx->ks_gemm)
+        return set_error(LVS_ERR_STATE, "lvs_ctx_set_ks_gemm_min: the tensor-core key switch is unavailable");
+    ctx->ks_gemm_min = min_jobs;
     return LVS_OK;
 }
 

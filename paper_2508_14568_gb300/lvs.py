@@ -37,7 +37,7 @@ EXPORTS = [
     "lvs_ctx_prepare_fft64", "lvs_pbs_batch_device_fft64", "lvs_noise_budget", "lvs_noise_plan",
     "lvs_ctx_autotune", "lvs_ctx_ks_plan", "lvs_ctx_set_ks_plan", "lvs_probe_int_mul", "lvs_preprocess_batch",
     "lvs_ct_string_pin", "lvs_ctx_br_split", "lvs_ctx_set_br_split",
-    "lvs_noise_pfail", "lvs_debug_fail_allocations",
+    "lvs_noise_pfail", "lvs_debug_fail_allocations", "lvs_ctx_ks_gemm_min", "lvs_ctx_set_ks_gemm_min",
     "lvs_server_create", "lvs_server_submit", "lvs_server_poll", "lvs_server_stats_get", "lvs_server_free",
 ]
 
@@ -140,6 +140,8 @@ def _declare(L):
         "lvs_ct_string_pin": ([vp], i32),
         "lvs_debug_fail_allocations": ([i32], None),
         "lvs_ctx_br_split": ([vp, ctypes.POINTER(sz)], i32),
+        "lvs_ctx_ks_gemm_min": ([vp, ctypes.POINTER(sz)], i32),
+        "lvs_ctx_set_ks_gemm_min": ([vp, sz], i32),
         "lvs_ctx_set_br_split": ([vp, sz], i32),
         "lvs_preprocess_batch": ([vp, vpp, sz, ctypes.c_char_p, sz, vpp], i32),
         "lvs_probe_int_mul": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
@@ -551,6 +553,16 @@ def lvs_ctx_ks_plan(ctx, njobs):
     a, b = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().lvs_ctx_ks_plan(ctx, njobs, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def lvs_ctx_ks_gemm_min(ctx):
+    v = ctypes.c_size_t()
+    _check(lib().lvs_ctx_ks_gemm_min(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def lvs_ctx_set_ks_gemm_min(ctx, min_jobs):
+    _check(lib().lvs_ctx_set_ks_gemm_min(ctx, min_jobs))
 
 
 def lvs_ctx_br_split(ctx):

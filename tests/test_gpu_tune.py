@@ -131,3 +131,46 @@ def test_autotune_sets_blind_rotation_split(full):
     ck, ctx, K = full
     L.lvs_ctx_autotune(ctx)
     assert 0 <= L.lvs_ctx_br_split(ctx) <= 152
+
+
+@pytest.mark.parametrize("which", ["test", "default"])
+def test_tensor_core_keyswitch_bit_exact(which):
+    """The key switch as bf16 GEMMs over the key's bytes (exact integer partial
+    sums) equals the oracle's key switch + modulus switch bit for bit, alone and
+    inside the edit-distance pipeline."""
+    params, oparams = (L.lvs_params_test(), T.params_test()) if which == "test" else \
+        (L.lvs_params_default(), T.params_lvs())
+    ck, sk = L.lvs_keygen(params, 6)
+    ctx = L.lvs_ctx_create(sk, 0)
+    K = T.Keys(oparams, 6)
+    p = K.params
+    big = K.big_dim
+    L.lvs_ctx_set_ks_gemm_min(ctx, 1)
+    assert L.lvs_ctx_ks_gemm_min(ctx) == 1
+    for count in (1, 17, 300):
+        cts = np.stack([T.encrypt(K, (7 * i) % 32, 15, 4, i) for i in range(count)])
+        want = np.stack([T.modswitch(K, T.keyswitch(K, c)) for c in cts])
+        d_in = torch.from_numpy(cts.view(np.int64)).cuda()
+        d_out = torch.zeros((count, p.n + 1), dtype=torch.int32, device="cuda")
+        L.lvs_keyswitch_batch_device(ctx, d_in, big + 1, d_out, count)
+        L.lvs_ctx_synchronize(ctx)
+        assert np.array_equal(d_out.cpu().numpy().view(np.uint32), want), count
+    if which == "test":
+        pairs = [("kitten", "sitting"), ("abc", "abd"), ("flaw", "lawn")]
+        A = [L.lvs_encrypt_string(ck, a, L.LVS_ALPHA_ASCII7, 16, 2 * k) for k, (a, b) in enumerate(pairs)]
+        B = [L.lvs_encrypt_string(ck, b, L.LVS_ALPHA_ASCII7, 16, 2 * k + 1) for k, (a, b) in enumerate(pairs)]
+        res = []
+        for m in (0, 1):
+            L.lvs_ctx_set_ks_gemm_min(ctx, m)
+            r = L.lvs_edit_distance_batch(ctx, A, B)
+            res.append([L.lvs_result_export(r, k, big) for k in range(len(pairs))])
+            assert L.lvs_decrypt_all(ck, r) == [P.wf_distance(a, b) for a, b in pairs]
+        for x, y in zip(*res):
+            assert np.array_equal(x, y)
+    L.lvs_ctx_free(ctx)
+
+
+def test_autotune_sets_keyswitch_gemm_threshold(full):
+    ck, ctx, K = full
+    L.lvs_ctx_autotune(ctx)
+    assert L.lvs_ctx_ks_gemm_min(ctx) in (0, 256, 1024, 4096)
