@@ -196,10 +196,14 @@ class _Handle:
         self.ptr = ptr
         self._owner = owner   # keeps parents alive
 
-    def __del__(self):
+    def close(self):
+        """Releases the native object now (idempotent)."""
         p, self.ptr = getattr(self, "ptr", None), None
         if p and self._free and _lib is not None:
             getattr(_lib, self._free)(p)
+
+    def __del__(self):
+        self.close()
 
     @property
     def _as_parameter_(self):
@@ -331,7 +335,7 @@ def lvs_ctx_create(sk, device=0, stream=None):
 
 def lvs_ctx_free(ctx):
     """Frees the context now (otherwise when the handle is collected)."""
-    ctx.__del__()
+    ctx.close()
 
 
 def lvs_ctx_synchronize(ctx):
@@ -522,7 +526,7 @@ def lvs_server_poll(server, ticket):
 
 def lvs_server_free(server):
     """Stops the server's worker and frees it now (otherwise when the handle is collected)."""
-    server.__del__()
+    server.close()
 
 
 def lvs_server_stats_get(server):
