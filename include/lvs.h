@@ -252,7 +252,8 @@ void lvs_eq_table_free(lvs_eq_table *t);
 /* Online phase of Section 5: distance of each preprocessed encrypted string
  * t[q] to the plaintext string plain[q] (plain_len[q] characters, all in the
  * table's subset).  EQ9[i][j] = T[b_j][i] is a device gather (0 PBS); one
- * cell PBS per cell. */
+ * cell PBS per cell.  opts as for lvs_edit_distance_batch (band: the result
+ * holds the readout path). */
 lvs_status lvs_edit_distance_preprocessed_batch(lvs_ctx *ctx, const lvs_eq_table *const *t,
                                                 const uint8_t *const *plain,
                                                 const size_t *plain_len, size_t n,

@@ -500,9 +500,9 @@ lvs_status lvs_edit_distance_preprocessed_batch(lvs_ctx *ctx, const lvs_eq_table
     lvs_opts o;
     lvs_opts_default(&o);
     if (opts) o = *opts;
-    if (o.band >= 0) return set_error(LVS_ERR_ARG, "banded mode is not available");
+    const bool banded = o.band >= 0;
     std::vector<PairRows> pairs(nq);
-    size_t vrows = 0, hrows = 0;
+    size_t vrows = 0, hrows = 0, trows = 0;
     for (size_t q = 0; q < nq; ++q) {
         if (!t[q] || (plain_len[q] && !plain[q])) return set_error(LVS_ERR_ARG, "NULL table or string");
         if (t[q]->P.p.N != ctx->P.p.N || t[q]->device != ctx->device)
@@ -518,6 +518,10 @@ lvs_status lvs_edit_distance_preprocessed_batch(lvs_ctx *ctx, const lvs_eq_table
         P.table_stride = t[q]->stride;
         P.row_of = t[q]->row_of;
         P.plain = plain[q];
+        if (banded) {
+            P.band = o.band;
+            trows += P.m + P.n;
+        }
         lvs_status st = plan_refresh(ctx, o.refresh_budget, P);
         if (st != LVS_OK) return st;
         vrows += P.m;
@@ -527,26 +531,35 @@ lvs_status lvs_edit_distance_preprocessed_batch(lvs_ctx *ctx, const lvs_eq_table
     std::lock_guard<std::mutex> lock(ctx->mu);
     for (size_t q = 0; q < nq; ++q)
         if (t[q]->done) LVS_CUDA(cudaStreamWaitEvent(ctx->stream, t[q]->done, 0));
+    // rows: [v][h][band taps]
     Arena A;
-    lvs_status st = arena_alloc(ctx, vrows + hrows, A);
+    lvs_status st = arena_alloc(ctx, vrows + hrows + trows, A);
     if (st != LVS_OK) return st;
-    size_t cv = 0, ch = vrows;
+    size_t cv = 0, ch = vrows, ct = vrows + hrows;
     for (auto &P : pairs) {
         P.v = cv; cv += P.m;
         P.h = ch; ch += P.n;
+        if (banded) { P.tap = ct; ct += P.m + P.n; }
     }
-    cudaError_t e = launch_fill_trivial(A.d, A.stride, ctx->P.big(), 0, vrows + hrows, 1ull << kDeltaLog, ctx->stream);
+    // OneMatrix boundary (and the band's path, whose out-of-band steps keep it)
+    cudaError_t e = launch_fill_trivial(A.d, A.stride, ctx->P.big(), 0, vrows + hrows + trows, 1ull << kDeltaLog,
+                                        ctx->stream);
     if (e != cudaSuccess) { arena_free(ctx, A); return cuda_error(e, "fill"); }
-    ctx->launches += vrows + hrows ? 1 : 0;
+    ctx->launches += vrows + hrows + trows ? 1 : 0;
     st = run_wavefront(ctx, pairs, A, o.use_graph != 0);
     if (st != LVS_OK) { arena_free(ctx, A); return st; }
     lvs_result *r = nullptr;
-    if ((st = make_result(ctx, hrows, &r)) != LVS_OK) { arena_free(ctx, A); return st; }
+    const size_t out_rows = banded ? trows : hrows;
+    if ((st = make_result(ctx, out_rows, &r)) != LVS_OK) { arena_free(ctx, A); return st; }
     size_t first = 0;
-    for (auto &P : pairs) { r->items.push_back({P.m, P.n, first, P.n, (long)P.m}); first += P.n; }
-    if (hrows) {
-        e = cudaMemcpy2DAsync(r->d, r->stride * 8, A.row(vrows), A.stride * 8, (ctx->P.big() + 1) * 8, hrows,
-                              cudaMemcpyDeviceToDevice, ctx->stream);
+    for (auto &P : pairs) {
+        const size_t cnt = banded ? P.m + P.n : P.n;
+        r->items.push_back({P.m, P.n, first, cnt, banded ? 0L : (long)P.m});
+        first += cnt;
+    }
+    if (out_rows) {
+        e = cudaMemcpy2DAsync(r->d, r->stride * 8, A.row(banded ? vrows + hrows : vrows), A.stride * 8,
+                              (ctx->P.big() + 1) * 8, out_rows, cudaMemcpyDeviceToDevice, ctx->stream);
         if (e != cudaSuccess) { arena_free(ctx, A); lvs_result_free(r); return cuda_error(e, "result copy"); }
     }
     arena_free(ctx, A);

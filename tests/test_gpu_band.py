@@ -124,3 +124,29 @@ def test_non_square_band_batch_mixed_lengths(small):
     r, d, npbs = _run(ck, ctx, pairs, P.ALPHA_ASCII7, band, 22)
     assert d == [P.wf_distance(a, b) for a, b in pairs]
     assert npbs == sum(3 * P.band_cells_general(len(a), len(b), band) for a, b in pairs)
+
+
+def test_preprocessed_path_with_band(small):
+    """The band (and its path readout) on the preprocessed path of Section 5:
+    exact from ceil(min(m,n)/2), the plaintext banded oracle otherwise."""
+    ck, ctx, _ = small
+    import random
+    rng = random.Random(33)
+    qs = [("".join(rng.choice(W.ALPHA27[:5]) for _ in range(rng.randint(2, 10))),
+           "".join(rng.choice(W.ALPHA27[:5]) for _ in range(rng.randint(2, 10)))) for _ in range(8)]
+    tables = L.lvs_preprocess_batch(ctx, [L.lvs_encrypt_string(ck, a, L.LVS_ALPHA_27, 34, k)
+                                          for k, (a, _) in enumerate(qs)])
+    for band in (1, 5):
+        pbs0 = L.lvs_ctx_pbs_count(ctx)
+        r = L.lvs_edit_distance_preprocessed_batch(ctx, tables, [b for _, b in qs], L.lvs_opts_default(band=band))
+        d = L.lvs_decrypt_all(ck, r)
+        want = []
+        for a, b in qs:
+            m, n = len(a), len(b)
+            E9 = [[9 if i and j and a[i - 1] == b[j - 1] else 0 for j in range(n + 1)] for i in range(m + 1)]
+            h, v = P.lvs_on_eq9(E9, m, n, band=band)
+            want.append(P.readout_path(h, v, m, n))
+        assert d == want
+        if band == 5:
+            assert d == [P.wf_distance(a, b) for a, b in qs]
+        assert L.lvs_ctx_pbs_count(ctx) - pbs0 == sum(P.band_cells_general(len(a), len(b), band) for a, b in qs)
