@@ -267,6 +267,17 @@ lvs_status lvs_result_info(const lvs_result *r, size_t *items, size_t pair, size
 lvs_status lvs_result_export(const lvs_result *r, size_t pair, uint64_t *dst, size_t *words);
 void lvs_result_free(lvs_result *r);
 
+/* Server-side readout (the return of Algorithm algo_complete on ciphertexts):
+ * a new result with one big LWE ciphertext per item of r, the sum of the
+ * item's rows plus the trivial encryption of its offset (m with the last row
+ * h[m][1..n], 0 with a band path), i.e. an encryption of the distance.  No
+ * bootstrap: the noise variance is at most that of m + n bootstrap outputs.
+ * The sum decodes to the distance with its padding bit clear only below 16, so
+ * every item must have max(m, n) <= 15; longer items, an lvs_eq result or a
+ * result of another context give LVS_ERR_ARG.  Asynchronous on ctx's stream,
+ * ordered after r; r may be freed afterwards.  Decrypt with lvs_decrypt. */
+lvs_status lvs_result_sum(lvs_ctx *ctx, const lvs_result *r, lvs_result **out);
+
 /* Client side: decrypts item `pair` to the edit distance m + sum_j h[m][j]
  * (each h decoded to {-1, 0, 1}); for an lvs_eq result, the decoded value. */
 lvs_status lvs_decrypt(const lvs_client_key *ck, const lvs_result *r, size_t pair, uint32_t *dist);

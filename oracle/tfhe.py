@@ -439,6 +439,19 @@ def decrypt_path(keys, cts, base=0):
     return base + sum(P.signed(decrypt(keys, c)) for c in cts)
 
 
+def readout_sum(keys, cts, base):
+    """The return of Algorithm algo_complete on ciphertexts: base (trivially
+    encrypted) + the sum of the difference ciphertexts, word by word mod 2^64.
+    It decrypts to the distance while that stays below 16 (5-bit plaintext
+    with its padding bit)."""
+    out = [0] * (keys.big_dim + 1)
+    for c in cts:
+        for t in range(keys.big_dim + 1):
+            out[t] = (out[t] + int(c[t])) % 2**64
+    out[-1] = (out[-1] + (int(base) % 32) * DELTA) % 2**64
+    return np.asarray(out, dtype=U64)
+
+
 def decrypt_distance(keys, h_row, m):
     """m + sum_j h[m][j], each h decrypted to {-1, 0, 1} (readout of Section 3.2
     with the boundary term taken once)."""

@@ -31,6 +31,7 @@ EXPORTS = [
     "lvs_ct_string_export", "lvs_ct_string_import", "lvs_decrypt_lwe", "lvs_encrypt_lwe", "lvs_eq",
     "lvs_edit_distance_batch", "lvs_preprocess", "lvs_eq_table_free",
     "lvs_edit_distance_preprocessed_batch", "lvs_result_info", "lvs_result_export", "lvs_result_free",
+    "lvs_result_sum",
     "lvs_decrypt", "lvs_decrypt_all", "lvs_pbs_batch_device", "lvs_keyswitch_batch_device",
     "lvs_poly_mul_device", "lvs_ctx_set_timing", "lvs_ctx_kernel_stats", "lvs_ctx_pbs_count",
     "lvs_ctx_launch_count", "lvs_ct_string_upload", "lvs_pbs_batch_device_noalloc",
@@ -131,6 +132,7 @@ def _declare(L):
         "lvs_result_info": ([vp, szp, sz, szp, szp], i32),
         "lvs_result_export": ([vp, sz, u64p, szp], i32),
         "lvs_result_free": ([vp], None),
+        "lvs_result_sum": ([vp, vp, vpp], i32),
         "lvs_decrypt": ([vp, vp, sz, u32p], i32),
         "lvs_decrypt_all": ([vp, vp, u32p], i32),
         "lvs_pbs_batch_device": ([vp, vp, sz, vp, vp, sz, sz], i32),
@@ -482,6 +484,12 @@ def lvs_result_export(r, pair, big_dim):
     a = np.zeros(w.value, np.uint64)
     _check(lib().lvs_result_export(r, pair, _u64p(a), ctypes.byref(w)))
     return a.reshape(-1, big_dim + 1)
+
+
+def lvs_result_sum(ctx, r):
+    out = ctypes.c_void_p()
+    _check(lib().lvs_result_sum(ctx, r, ctypes.byref(out)))
+    return Result(out.value)
 
 
 def lvs_decrypt(ck, r, pair):

@@ -299,3 +299,25 @@ def test_lvs_encrypted_band_exact_skip_and_approx(keys):
         if band >= m // 2:
             assert want == P.wf_distance(a, b)
         assert res["pbs"] == 3 * P.band_cells(m, band)
+
+
+def test_readout_sum_decrypts_to_distance(keys):
+    """The return of Algorithm algo_complete taken on ciphertexts (one LWE
+    sum, no bootstrap) decrypts to Wagner-Fischer, for the last-row readout
+    (base m) and the band path (base 0)."""
+    for a, b, band in [("kitten", "sitting", None), ("abcd", "ab", None), ("flaw", "lawn", 1), ("GATT", "ACA", 0)]:
+        alpha = P.ALPHA_DNA4 if a.isupper() else P.ALPHA_ASCII7
+        xa = T.encrypt_string(keys, a, alpha, 41, 0)
+        yb = T.encrypt_string(keys, b, alpha, 41, 1)
+        res = T.lvs_encrypted(keys, xa, yb, alpha, parallel=True, band=band)
+        if band is None:
+            got = T.decrypt(keys, T.readout_sum(keys, res["h_row"], len(a)))
+            assert got == P.wf_distance(a, b) == T.decrypt_distance(keys, res["h_row"], len(a))
+        else:
+            got = T.decrypt(keys, T.readout_sum(keys, res["path"], 0))
+            assert got == T.decrypt_path(keys, res["path"])
+    # a planted off-by-one base is seen
+    xa = T.encrypt_string(keys, "ab", P.ALPHA_ASCII7, 42, 0)
+    yb = T.encrypt_string(keys, "ba", P.ALPHA_ASCII7, 42, 1)
+    res = T.lvs_encrypted(keys, xa, yb, P.ALPHA_ASCII7, parallel=True)
+    assert T.decrypt(keys, T.readout_sum(keys, res["h_row"], 3)) != P.wf_distance("ab", "ba")
