@@ -641,6 +641,7 @@ void lvs_result_free(lvs_result *r)
     if (!r) return;
     cudaSetDevice(r->device);
     if (r->done) { cudaEventSynchronize(r->done); cudaEventDestroy(r->done); }
+    // cudaFree waits for the device, so work still reading r (lvs_result_sum) ends first
     if (r->d) cudaFree(r->d);
     cudaGetLastError();
     delete r;
