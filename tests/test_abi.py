@@ -124,3 +124,21 @@ def test_context_without_gpu_fails_loudly():
     with pytest.raises(L.LvsError) as e:
         L.lvs_ctx_create(sk, 0)
     assert e.value.status == L.LVS_ERR_CUDA
+
+
+def test_null_arguments_are_rejected_before_any_device_work():
+    """Entry points that launch work check their pointers on the host first:
+    LVS_ERR_ARG and a message, no CUDA call (this runs without a GPU)."""
+    lib = L.lib()
+    out = ctypes.c_void_p()
+    u = ctypes.c_uint32()
+    calls = [
+        ("lvs_result_sum", lambda: lib.lvs_result_sum(None, None, ctypes.byref(out))),
+        ("lvs_edit_distance_batch", lambda: lib.lvs_edit_distance_batch(None, None, None, 1, None, ctypes.byref(out))),
+        ("lvs_decrypt", lambda: lib.lvs_decrypt(None, None, 0, ctypes.byref(u))),
+        ("lvs_decrypt_all", lambda: lib.lvs_decrypt_all(None, None, None)),
+    ]
+    for name, call in calls:
+        assert call() == L.LVS_ERR_ARG, name
+        assert lib.lvs_last_error().decode(), name
+        assert out.value is None
