@@ -149,13 +149,16 @@ def balanced_digit_sq(base_log):
     return (B * B + 2) / 12.0
 
 
-def var_pbs(p):
+def var_pbs(p, weight_lwe=None, weight_glwe=None):
     """Output of the blind rotation + sample extract: gadget rounding of
-    X^a ACC - ACC in each of the n CMux (weight: expected 1 + |S| of the
-    GLWE key, per expected set bit of the LWE key) plus the BSK noise."""
+    X^a ACC - ACC in each CMux whose LWE key bit is set (weight_lwe of them,
+    expected n/2), seen through the body and the GLWE key (1 + weight_glwe
+    set coefficients, expected kN/2), plus the BSK noise of every CMux."""
     beta = p["pbs_level"] * p["pbs_base_log"]
     rounding = (2.0 ** (63 - beta)) ** 2 / 3.0
-    weight = (p["n"] / 2.0) * (1.0 + p["k"] * p["N"] / 2.0)
+    w_lwe = p["n"] / 2.0 if weight_lwe is None else float(weight_lwe)
+    w_glwe = p["k"] * p["N"] / 2.0 if weight_glwe is None else float(weight_glwe)
+    weight = w_lwe * (1.0 + w_glwe)
     bsk = (p["n"] * (p["k"] + 1) * p["pbs_level"] * p["N"] * balanced_digit_sq(p["pbs_base_log"])
            * tuniform_variance(p["glwe_noise_log2"]))
     return weight * rounding + bsk

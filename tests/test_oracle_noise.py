@@ -173,3 +173,61 @@ def test_output_variances_closed_form():
     for (i, j), (vv, vh) in out.items():
         assert vh == (2 * j - 1 if i >= j else 2 * i)
         assert vv == (2 * i - 1 if j >= i else 2 * j)
+
+
+def test_pbs_output_variance_model(keys):
+    """var_pbs (Section 2.2's bootstrap noise) against the oracle's own
+    bootstraps: the phase error of 768 PBS outputs, with the keys' actual
+    weights, has the predicted variance (the gadget rounding term dominates at
+    this parameter set, the key-noise term is checked by the full-size GPU
+    measurement)."""
+    p = keys.params
+    pd = p.as_dict()
+    count = 768
+    msgs = [t % 16 for t in range(count)]
+    lut = [(3 * x + 1) % 16 for x in range(16)]
+    cts = np.stack([T.encrypt(keys, m, 91, 4, t) for t, m in enumerate(msgs)])
+    out = T.pbs_many(keys, cts, np.tile(np.asarray(lut, np.uint32), (count, 1)))
+    err = np.array([_signed(T.phase(keys, out[t]) - lut[m] * T.DELTA) for t, m in enumerate(msgs)],
+                   dtype=np.float64)
+    w_lwe, w_glwe = int(np.sum(keys.lwe_key)), int(np.sum(keys.glwe_key))
+    ratio = np.mean(err ** 2) / Nz.var_pbs(pd, w_lwe, w_glwe)
+    assert 0.8 < ratio < 1.2, ratio
+    # the expected-weight form is the same model at weights n/2 and kN/2
+    assert Nz.var_pbs(pd) == Nz.var_pbs(pd, p.n / 2, p.k * p.N / 2)
+
+
+def test_modswitch_body_term():
+    """A ciphertext with a zero mask leaves only the body's rounding to a
+    multiple of 2^64 / 2N: variance step^2 / 12, the weight-0 case of the
+    modulus-switch model."""
+    K = T.Keys(T.params_test(), 2)
+    p = K.params
+    step = 2**64 // (2 * p.N)
+    rng = np.random.default_rng(5)
+    bodies = rng.integers(0, 2**63, size=4000, dtype=np.int64).astype(np.uint64) * np.uint64(2) + \
+        rng.integers(0, 2, size=4000, dtype=np.int64).astype(np.uint64)
+    err = []
+    for b in bodies:
+        small = np.zeros(p.n + 1, dtype=np.uint64)
+        small[-1] = b
+        ms = T.modswitch(K, small)
+        assert not ms[:-1].any()
+        err.append(_signed(int(ms[-1]) * step - int(b)))
+    ratio = np.mean(np.array(err, dtype=np.float64) ** 2) / Nz.var_modswitch(p.as_dict(), 0)
+    assert 0.93 < ratio < 1.07, ratio
+
+
+@pytest.mark.parametrize("level,base_log", [(1, 3), (2, 3), (5, 3), (2, 4), (3, 5)])
+def test_balanced_digit_second_moment_by_enumeration(level, base_log):
+    """Every value of the top level * base_log bits, decomposed by the oracle:
+    all digits lie in [-B/2, B/2) and their mean square is the model's E[d^2]."""
+    beta = level * base_log
+    B = 2 ** base_log
+    sq, cnt = 0, 0
+    for v in range(2 ** beta):
+        d = T.decompose(v << (64 - beta), level, base_log)
+        assert all(-B // 2 <= x < B // 2 for x in d)
+        sq += sum(x * x for x in d)
+        cnt += level
+    assert abs(sq / cnt - Nz.balanced_digit_sq(base_log)) < 1e-12
