@@ -262,8 +262,8 @@ lvs_status lvs_edit_distance_preprocessed_batch(lvs_ctx *ctx, const lvs_eq_table
 /* Number of items in a result, and for item `pair`: m and n. */
 lvs_status lvs_result_info(const lvs_result *r, size_t *items, size_t pair, size_t *m, size_t *n);
 /* Copies the ciphertexts of item `pair` (n big LWE ciphertexts; m + n with a
- * band; 1 for lvs_eq) to host memory dst ([rows][k*N+1]).  dst = NULL: size
- * query in *words. */
+ * band; 1 for lvs_eq and lvs_result_sum) to host memory dst ([rows][k*N+1]).
+ * dst = NULL: size query in *words. */
 lvs_status lvs_result_export(const lvs_result *r, size_t pair, uint64_t *dst, size_t *words);
 void lvs_result_free(lvs_result *r);
 
@@ -279,7 +279,9 @@ void lvs_result_free(lvs_result *r);
 lvs_status lvs_result_sum(lvs_ctx *ctx, const lvs_result *r, lvs_result **out);
 
 /* Client side: decrypts item `pair` to the edit distance m + sum_j h[m][j]
- * (each h decoded to {-1, 0, 1}); for an lvs_eq result, the decoded value. */
+ * (each h decoded to {-1, 0, 1}; with a band, the sum along the readout path;
+ * for an lvs_result_sum result, the one decoded sum); for an lvs_eq result,
+ * the decoded value. */
 lvs_status lvs_decrypt(const lvs_client_key *ck, const lvs_result *r, size_t pair, uint32_t *dist);
 /* Decrypts every item of a result; dist has room for `items` values. */
 lvs_status lvs_decrypt_all(const lvs_client_key *ck, const lvs_result *r, uint32_t *dist);
