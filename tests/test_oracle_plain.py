@@ -242,6 +242,13 @@ def test_preprocessed_plain_equals_wf():
         b = "".join(rng.choice(pool) for _ in range(rng.randint(1, 12)))
         t = P.preprocess_table(a, pool, P.ALPHA_27)
         assert P.lvs_preprocessed_plain(t, b, len(a)) == P.wf_distance(a, b)
+    # DNA: the one-lookup table of Section 6.3
+    for _ in range(100):
+        a = "".join(rng.choice("ACGT") for _ in range(rng.randint(1, 12)))
+        b = "".join(rng.choice("ACGT") for _ in range(rng.randint(1, 12)))
+        t = P.preprocess_table(a, "ACGT", P.ALPHA_DNA4)
+        assert all(x in (0, 9) for col in t.values() for x in col)
+        assert P.lvs_preprocessed_plain(t, b, len(a)) == P.wf_distance(a, b)
 
 
 def _e9(a, b):
@@ -307,3 +314,17 @@ def test_table_tab_pbs_band_rows():
     approx_q = 3 * P.band_cells(m, l)
     assert approx_q == 6 * l * m + 3 * m - 3 * l * l - 3 * l
     assert abs(approx_q / (6 * l * m) - 1) < 0.15
+
+
+def test_general_band_cell_count_by_path_cost():
+    """band_cells_general counts the cells through which an edit path costs at
+    most |n - m| + 2 band (|k| to reach diagonal k = j - i, |n - m - k| to get
+    back), the characterisation of the widened band; every cell once the band
+    covers the longer string."""
+    for m in range(1, 9):
+        for n in range(1, 9):
+            for band in range(0, 5):
+                want = sum(1 for i in range(1, m + 1) for j in range(1, n + 1)
+                           if abs(j - i) + abs((n - m) - (j - i)) <= abs(n - m) + 2 * band)
+                assert P.band_cells_general(m, n, band) == want, (m, n, band)
+            assert P.band_cells_general(m, n, max(m, n)) == m * n
