@@ -27,6 +27,27 @@ import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+
+# The paper's own figures, quoted beside ours as context only: CPU (dual AMD
+# EPYC 9174F, 32 cores / 64 threads, TFHE-rs v0.7.2 with its "4-bit message,
+# 0-bit carry" parameters, Section 6.2), another machine and another parameter
+# set, so no ratio to them is taken.
+PAPER_CONTEXT = {
+    "hardware": "2x AMD EPYC 9174F (32 cores, 64 threads), TFHE-rs v0.7.2, 4-bit message / 0-bit carry set",
+    # Table tab_lat: Leuvenshtein Exact, one thread, m = n = 100 in 7 min 19 s (3 PBS per cell)
+    "exact_1_thread_m100_cells_per_s": round(100 * 100 / 439.0, 1),
+    "exact_1_thread_m100_pbs_per_s": round(3 * 100 * 100 / 439.0, 1),
+    # Table table:results_parallel: 64 distances in a batch, 14.7 s per distance amortised
+    "exact_64_threads_m100_cells_per_s": round(100 * 100 / 14.7, 1),
+    # Table tab_unenc: preprocessed online phase, m = n = 256 in 950 s (1 PBS per cell)
+    "preprocessed_1_thread_m256_cells_per_s": round(256 * 256 / 950.0, 1),
+    "speedups_claimed": {
+        "vs_concrete_m256_exact_skip": "278x (Table tab_lat)",
+        "vs_wagner_fischer_on_tfhe_rs": "39-40x (Table tab_lat, Section 1.1)",
+        "preprocessing_online": "3x (Table tab_unenc)",
+        "batching_64_threads": "~32x (Table table:results_parallel)",
+    },
+}
 sys.path.insert(0, ROOT)
 
 SM_COUNT_NOMINAL = 152
@@ -523,6 +544,7 @@ def run_lvs(args):
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "paper_context": PAPER_CONTEXT,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
