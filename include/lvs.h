@@ -211,6 +211,46 @@ lvs_status lvs_noise_pfail(const lvs_params *p, double key_var, double *log2_pfa
 lvs_status lvs_noise_plan(size_t m, size_t n, int32_t band, double budget, uint8_t *refresh,
                           double *max_key_var);
 
+/* The wavefront plan of one pair, exactly as the distance calls build it,
+ * exported for inspection (host only, no GPU).  Rows are indices into the
+ * pair's working rows, laid out as
+ *   encrypted reference (eq_lookups = 1 or 2): [a: m*C][b: n*C][v: m][h: n]
+ *       [band path: m + n][EQ1 ring: 2m, C = 2 only][EQ9 ring: 2m]
+ *   plaintext reference (eq_lookups = 0): [table: nsub*m][v: m][h: n]
+ *       [band path: m + n]
+ * with C = eq_lookups symbols per character (row a + (i-1)*C + symbol), table
+ * row T[k][i] at k*m + i - 1 (k the position of the symbol in subset), v[i] at
+ * v + i - 1, h[j] at h + j - 1, and ring slot (d & 1) * m + i - 1 for
+ * anti-diagonal d = i + j - 2.  Launch step s holds, for C = 2, the EQ1
+ * lookups of anti-diagonal s, the EQ9 lookups of s - 1 and the cells of
+ * s - 2; for C = 1 the EQ9 lookups of s and the cells of s - 1; for the
+ * plaintext reference the cells of s (Section 6.2's parallelism over the
+ * cells of an anti-diagonal).
+ * Arguments: band as lvs_opts.band; refresh NULL or m + n + 1 bytes as from
+ * lvs_noise_plan; plain / subset (nsub symbols, distinct, covering plain) for
+ * the plaintext reference, else NULL.  layout (may be NULL) receives the first
+ * row of each block (-1 if absent) and the total.  jobs (may be NULL): room
+ * for *count entries; on return *count is the number of jobs (LVS_ERR_ARG if
+ * the room was too small, nothing written). */
+typedef struct lvs_plan_layout {
+    int64_t a, b, v, h, path, eq1, eq9, table, rows, steps;
+} lvs_plan_layout;
+typedef struct lvs_plan_job {
+    int64_t step;
+    int64_t src[3];      /* input rows, -1 if unused                         */
+    int64_t coef[3];     /* input = sum coef * src + cst (times Delta)       */
+    int64_t cst;
+    int64_t dst[2];      /* rows written: the lookup (store), or v and h (cell) */
+    int64_t tap;         /* band path row receiving a copy, -1 if none       */
+    int32_t lut;         /* 0 EQ, 1 EQ9, 2 MIN, 3 V                          */
+    int32_t kind;        /* 0 store, 1 cell: v = M - h_old, h = M - v_old    */
+    int32_t tapsel;      /* store: 1 copies the output; cell: 1 new v, 2 new h */
+    int32_t pad;
+} lvs_plan_job;
+lvs_status lvs_plan_pair(size_t m, size_t n, uint32_t eq_lookups, int32_t band, const uint8_t *refresh,
+                         const uint8_t *plain, const uint8_t *subset, size_t nsub, lvs_plan_layout *layout,
+                         lvs_plan_job *jobs, size_t *count);
+
 /* Encrypted equality of characters a[i] and b[j] (Algorithm alg_ascii: 2 PBS
  * for ASCII7 / 27 symbols; Section 4.1: 1 PBS for DNA4).  times9 != 0 gives
  * enc(9*EQ) (Eq. eq_eqlut9), else enc(EQ).  The result holds one ciphertext. */

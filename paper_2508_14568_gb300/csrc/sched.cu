@@ -491,6 +491,96 @@ void lvs_eq_table_free(lvs_eq_table *t)
     delete t;
 }
 
+lvs_status lvs_plan_pair(size_t m, size_t n, uint32_t eq_lookups, int32_t band, const uint8_t *refresh,
+                         const uint8_t *plain, const uint8_t *subset, size_t nsub, lvs_plan_layout *layout,
+                         lvs_plan_job *jobs, size_t *count)
+{
+    if (!count) return set_error(LVS_ERR_ARG, "lvs_plan_pair: NULL count");
+    if (eq_lookups > 2) return set_error(LVS_ERR_ARG, "lvs_plan_pair: eq_lookups must be 0, 1 or 2");
+    const bool pre = eq_lookups == 0;
+    if (pre && n && (!plain || !subset || nsub == 0))
+        return set_error(LVS_ERR_ARG, "lvs_plan_pair: the plaintext reference needs plain and subset");
+    PairRows P;
+    P.m = m;
+    P.n = n;
+    P.C = pre ? 1 : eq_lookups;
+    P.band = band >= 0 ? band : -1;
+    if (refresh) P.refresh.assign(refresh, refresh + m + n + 1);
+    int32_t row_of[256];
+    std::fill(row_of, row_of + 256, -1);
+    if (pre)
+        for (size_t k = 0; k < nsub; ++k) {
+            if (row_of[subset[k]] >= 0) return set_error(LVS_ERR_ARG, "lvs_plan_pair: repeated subset symbol");
+            row_of[subset[k]] = (int32_t)k;
+        }
+    if (pre)
+        for (size_t j = 0; j < n; ++j)
+            if (row_of[plain[j]] < 0) return set_error(LVS_ERR_ARG, "lvs_plan_pair: plain symbol outside the subset");
+    lvs_plan_layout L;
+    L.a = L.b = L.path = L.eq1 = L.eq9 = L.table = -1;
+    size_t r = 0;
+    if (pre) { L.table = 0; r += nsub * m; }
+    else { L.a = (int64_t)r; r += m * P.C; L.b = (int64_t)r; r += n * P.C; }
+    L.v = (int64_t)r; r += m;
+    L.h = (int64_t)r; r += n;
+    if (P.band >= 0) { L.path = (int64_t)r; r += m + n; }
+    if (!pre) {
+        if (P.C == 2) { L.eq1 = (int64_t)r; r += 2 * m; }
+        L.eq9 = (int64_t)r; r += 2 * m;
+    }
+    L.rows = (int64_t)r;
+    // one word per row: a row's index is its offset from the base
+    std::vector<uint64_t> base(r + 1);
+    Arena A;
+    A.d = base.data();
+    A.stride = 1;
+    A.rows = r;
+    if (!pre) { P.x = (size_t)L.a; P.y = (size_t)L.b; }
+    P.v = (size_t)L.v;
+    P.h = (size_t)L.h;
+    if (P.band >= 0) P.tap = (size_t)L.path;
+    if (!pre) {
+        if (P.C == 2) P.eq1 = (size_t)L.eq1;
+        P.eq9 = (size_t)L.eq9;
+    } else {
+        P.table = A.row(0);
+        P.table_stride = 1;
+        P.row_of = row_of;
+        P.plain = plain;
+    }
+    const long steps = pair_steps(P);
+    L.steps = steps;
+    std::vector<Job> J;
+    std::vector<int64_t> step_of;
+    for (long st = 0; st < steps; ++st) {
+        plan_pair_step(P, A, st, J);
+        step_of.resize(J.size(), st);
+    }
+    if (layout) *layout = L;
+    const size_t room = *count;
+    *count = J.size();
+    if (!jobs) return LVS_OK;
+    if (room < J.size()) return set_error(LVS_ERR_ARG, "lvs_plan_pair: jobs has too little room");
+    auto row = [&](const uint64_t *q) -> int64_t { return q ? (int64_t)(q - A.d) : -1; };
+    for (size_t k = 0; k < J.size(); ++k) {
+        lvs_plan_job &o = jobs[k];
+        o.step = step_of[k];
+        for (int t = 0; t < 3; ++t) {
+            o.src[t] = row(J[k].src[t]);
+            o.coef[t] = J[k].src[t] ? J[k].coef[t] : 0;
+        }
+        o.cst = J[k].cst;
+        o.dst[0] = row(J[k].dst[0]);
+        o.dst[1] = row(J[k].dst[1]);
+        o.tap = J[k].tapsel ? row(J[k].tap) : -1;
+        o.lut = J[k].lut;
+        o.kind = J[k].kind;
+        o.tapsel = J[k].tapsel;
+        o.pad = 0;
+    }
+    return LVS_OK;
+}
+
 lvs_status lvs_edit_distance_preprocessed_batch(lvs_ctx *ctx, const lvs_eq_table *const *t, const uint8_t *const *plain,
                                                 const size_t *plain_len, size_t nq, const lvs_opts *opts,
                                                 lvs_result **out)

@@ -31,7 +31,7 @@ EXPORTS = [
     "lvs_ct_string_export", "lvs_ct_string_import", "lvs_decrypt_lwe", "lvs_encrypt_lwe", "lvs_eq",
     "lvs_edit_distance_batch", "lvs_preprocess", "lvs_eq_table_free",
     "lvs_edit_distance_preprocessed_batch", "lvs_result_info", "lvs_result_export", "lvs_result_free",
-    "lvs_result_sum",
+    "lvs_result_sum", "lvs_plan_pair",
     "lvs_decrypt", "lvs_decrypt_all", "lvs_pbs_batch_device", "lvs_keyswitch_batch_device",
     "lvs_poly_mul_device", "lvs_ctx_set_timing", "lvs_ctx_kernel_stats", "lvs_ctx_pbs_count",
     "lvs_ctx_launch_count", "lvs_ct_string_upload", "lvs_pbs_batch_device_noalloc",
@@ -75,6 +75,20 @@ class lvs_server_stats(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class lvs_plan_layout(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("a", "b", "v", "h", "path", "eq1", "eq9", "table", "rows", "steps")]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class lvs_plan_job(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("src", ctypes.c_int64 * 3), ("coef", ctypes.c_int64 * 3),
+                ("cst", ctypes.c_int64), ("dst", ctypes.c_int64 * 2), ("tap", ctypes.c_int64),
+                ("lut", ctypes.c_int32), ("kind", ctypes.c_int32), ("tapsel", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class lvs_kernel_stats(ctypes.Structure):
@@ -153,6 +167,8 @@ def _declare(L):
         "lvs_noise_pfail": ([ctypes.POINTER(lvs_params), ctypes.c_double, ctypes.POINTER(ctypes.c_double)], i32),
         "lvs_noise_plan": ([sz, sz, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_uint8),
                             ctypes.POINTER(ctypes.c_double)], i32),
+        "lvs_plan_pair": ([sz, sz, u32, i32, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, sz,
+                           ctypes.POINTER(lvs_plan_layout), ctypes.POINTER(lvs_plan_job), szp], i32),
         "lvs_keyswitch_batch_device": ([vp, vp, sz, vp, sz], i32),
         "lvs_poly_mul_device": ([vp, vp, vp, vp, sz], i32),
         "lvs_ctx_set_timing": ([vp, i32], i32),
@@ -288,6 +304,22 @@ def lvs_noise_plan(m, n, band, budget):
     _check(lib().lvs_noise_plan(m, n, band, ctypes.c_double(budget),
                                 r.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.byref(w)))
     return [int(d) for d in np.nonzero(r)[0]], w.value
+
+
+def lvs_plan_pair(m, n, eq_lookups, band=-1, refresh=None, plain=None, subset=None):
+    """(layout dict, list of job dicts) of one pair's wavefront plan (host only)."""
+    rf = bytes(bytearray(refresh)) if refresh is not None else None
+    pb = _bytes(plain) if plain is not None else None
+    sb = _bytes(subset) if subset is not None else None
+    lay = lvs_plan_layout()
+    cnt = ctypes.c_size_t(0)
+    args = (m, n, eq_lookups, band, rf, pb, sb, len(sb) if sb is not None else 0, ctypes.byref(lay))
+    _check(lib().lvs_plan_pair(*args, None, ctypes.byref(cnt)))
+    jobs = (lvs_plan_job * max(1, cnt.value))()
+    _check(lib().lvs_plan_pair(*args, jobs, ctypes.byref(cnt)))
+    out = [{"step": j.step, "src": list(j.src), "coef": list(j.coef), "cst": j.cst, "dst": list(j.dst),
+            "tap": j.tap, "lut": j.lut, "kind": j.kind, "tapsel": j.tapsel} for j in jobs[:cnt.value]]
+    return lay.as_dict(), out
 
 
 def lvs_version():
