@@ -139,6 +139,13 @@ def test_refreshed_plan_computes_wf():
         extra = sum(1 for i in range(1, m + 1) for j in range(1, n + 1) if refresh[i + j])
         assert len(jobs) == 3 * m * n + extra
         assert sum(1 for j in jobs if j["lut"] == 3) == 2 * extra
+        # with a band: the refreshed cells on the readout path feed it too
+        band = 2
+        diags, _ = L.lvs_noise_plan(m, n, band, 40.0)
+        refresh = [1 if d in diags else 0 for d in range(m + n + 1)]
+        d, lay, jobs = simulate(a, b, P.ALPHA_ASCII7, band=band, refresh=refresh)
+        h, v = P.lvs_on_eq9(_e9(a, b), m, n, band=band)
+        assert d == P.readout_path(h, v, m, n), (a, b, diags)
 
 
 def test_preprocessed_plan_computes_wf():
