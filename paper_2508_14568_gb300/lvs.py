@@ -271,8 +271,10 @@ def lvs_params_test():
 
 
 def lvs_opts_default(use_graph=True, band=-1, refresh_budget=0):
-    """band >= 0: only cells with |i - j| <= band (pairs with m = n);
-    refresh_budget: 0 from the parameters, > 0 explicit, < 0 no refresh."""
+    """band >= 0: only the cells of the band of Section 3.2 (|i - j| <= band,
+    widened to the diagonals between 0 and n - m when m != n), the result
+    holding the readout path; refresh_budget: 0 from the parameters, > 0
+    explicit, < 0 no refresh."""
     o = lvs_opts()
     lib().lvs_opts_default(ctypes.byref(o))
     o.use_graph = 1 if use_graph else 0
