@@ -465,6 +465,13 @@ lvs_status lvs_ctx_set_br_split(lvs_ctx *ctx, size_t max_jobs);
  * the context could not set it up (it then uses the kernel for every size). */
 lvs_status lvs_ctx_ks_gemm_min(lvs_ctx *ctx, size_t *min_jobs);
 lvs_status lvs_ctx_set_ks_gemm_min(lvs_ctx *ctx, size_t min_jobs);
+/* Wavefront steps (and PBS batches) wider than max_jobs PBS run as several
+ * launches in sequence: bounded launch time and scratch.  The two lookups of
+ * a refreshed cell always share a launch (the second reads the v row the
+ * first one writes).  Default 65536; max_jobs in [2, 2^20], 0 restores the
+ * default (LVS_ERR_ARG otherwise).  Same results bit for bit. */
+lvs_status lvs_ctx_max_launch_jobs(lvs_ctx *ctx, size_t *max_jobs);
+lvs_status lvs_ctx_set_max_launch_jobs(lvs_ctx *ctx, size_t max_jobs);
 
 /* Test hook (host-side fault injection, no counterpart in the paper): the
  * next `count` allocations of batch / query device memory fail as if the

@@ -140,15 +140,31 @@ static lvs_status launch_step(lvs_ctx *ctx, const Job *d_jobs, size_t nj, bool t
     return LVS_OK;
 }
 
-// A step wider than this runs as several launches (its jobs are independent):
-// bounded launch time and modulus-switch scratch.
+// A step wider than ctx->max_launch_jobs runs as several launches: bounded
+// launch time and modulus-switch scratch.
 constexpr size_t kMaxLaunchJobs = 1u << 16;
+
+// End of the launch that starts at job c0 of a step ending at e.  The jobs of
+// a step are independent except the two lookups of a refreshed cell (v through
+// LUT_V, then h through LUT_V from the swapped key): the second reads the v row
+// the first one writes, so both must share a launch, whose key switch gathers
+// every input before its blind rotation writes.
+static size_t chunk_end(const lvs_ctx *ctx, const std::vector<Job> &jobs, size_t c0, size_t e)
+{
+    size_t c1 = std::min(e, c0 + ctx->max_launch_jobs);
+    if (c1 < e && c1 - c0 > 1) {
+        const Job &a = jobs[c1 - 1], &b = jobs[c1];
+        if (a.lut == LUT_V && b.lut == LUT_V && a.dst[0] == a.src[0] && a.src[0] == b.src[0] && a.src[1] == b.src[1])
+            --c1;
+    }
+    return c1;
+}
 
 lvs_status run_steps(lvs_ctx *ctx, const std::vector<Job> &jobs, const std::vector<size_t> &off, bool use_graph)
 {
     size_t widest = 0;
     for (size_t s = 0; s + 1 < off.size(); ++s) widest = std::max(widest, off[s + 1] - off[s]);
-    widest = std::min(widest, kMaxLaunchJobs);
+    widest = std::min(widest, ctx->max_launch_jobs);
     if (jobs.empty()) return LVS_OK;
     // NVTX range around the whole run (visible to nsys / ncu when attached; a
     // no-op otherwise)
@@ -171,8 +187,10 @@ lvs_status run_steps(lvs_ctx *ctx, const std::vector<Job> &jobs, const std::vect
         LVS_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
         lvs_status lst = LVS_OK;
         for (size_t s = 0; s + 1 < off.size() && lst == LVS_OK; ++s)
-            for (size_t c0 = off[s]; c0 < off[s + 1] && lst == LVS_OK; c0 += kMaxLaunchJobs)
-                lst = launch_step(ctx, ctx->jobs + c0, std::min(kMaxLaunchJobs, off[s + 1] - c0), false);
+            for (size_t c0 = off[s], c1; c0 < off[s + 1] && lst == LVS_OK; c0 = c1) {
+                c1 = chunk_end(ctx, jobs, c0, off[s + 1]);
+                lst = launch_step(ctx, ctx->jobs + c0, c1 - c0, false);
+            }
         cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
         if (lst != LVS_OK) { if (graph) cudaGraphDestroy(graph); return lst; }
         if (ce != cudaSuccess) return cuda_error(ce, "cudaStreamEndCapture");
@@ -188,8 +206,9 @@ lvs_status run_steps(lvs_ctx *ctx, const std::vector<Job> &jobs, const std::vect
         ctx->graphs.push_back({exec, done});
     } else {
         for (size_t s = 0; s + 1 < off.size(); ++s)
-            for (size_t c0 = off[s]; c0 < off[s + 1]; c0 += kMaxLaunchJobs) {
-                st = launch_step(ctx, ctx->jobs + c0, std::min(kMaxLaunchJobs, off[s + 1] - c0), timed);
+            for (size_t c0 = off[s], c1; c0 < off[s + 1]; c0 = c1) {
+                c1 = chunk_end(ctx, jobs, c0, off[s + 1]);
+                st = launch_step(ctx, ctx->jobs + c0, c1 - c0, timed);
                 if (st != LVS_OK) return st;
             }
     }
@@ -233,6 +252,7 @@ lvs_status lvs_ctx_create(const lvs_server_key *sk, int device, void *stream, lv
     // to one ciphertext per three SMs (lvs_ctx_autotune measures the crossover)
     ctx->br_clusters = br_cluster_capacity(N);
     ctx->br_split_max = ctx->br_clusters > 0 ? (size_t)(ctx->num_sms / 3) : 0;
+    ctx->max_launch_jobs = kMaxLaunchJobs;
 
     std::vector<uint32_t> tw;
     make_twiddles(N, tw);

@@ -210,6 +210,24 @@ lvs_status lvs_ctx_set_ks_gemm_min(lvs_ctx *ctx, size_t min_jobs)
     return LVS_OK;
 }
 
+lvs_status lvs_ctx_max_launch_jobs(lvs_ctx *ctx, size_t *max_jobs)
+{
+    if (!ctx || !max_jobs) return set_error(LVS_ERR_ARG, "lvs_ctx_max_launch_jobs: NULL argument");
+    *max_jobs = ctx->max_launch_jobs;
+    return LVS_OK;
+}
+
+lvs_status lvs_ctx_set_max_launch_jobs(lvs_ctx *ctx, size_t max_jobs)
+{
+    if (!ctx) return set_error(LVS_ERR_ARG, "lvs_ctx_set_max_launch_jobs: NULL context");
+    if (max_jobs == 0) max_jobs = (size_t)1 << 16;
+    if (max_jobs < 2 || max_jobs > ((size_t)1 << 20))
+        return set_error(LVS_ERR_ARG, "lvs_ctx_set_max_launch_jobs: max_jobs must be in [2, 2^20]");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->max_launch_jobs = max_jobs;
+    return LVS_OK;
+}
+
 lvs_status lvs_ctx_br_split(lvs_ctx *ctx, size_t *max_jobs)
 {
     if (!ctx || !max_jobs) return set_error(LVS_ERR_ARG, "lvs_ctx_br_split: NULL argument");

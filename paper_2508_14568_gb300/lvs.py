@@ -31,7 +31,7 @@ EXPORTS = [
     "lvs_ct_string_export", "lvs_ct_string_import", "lvs_decrypt_lwe", "lvs_encrypt_lwe", "lvs_eq",
     "lvs_edit_distance_batch", "lvs_preprocess", "lvs_eq_table_free",
     "lvs_edit_distance_preprocessed_batch", "lvs_result_info", "lvs_result_export", "lvs_result_free",
-    "lvs_result_sum", "lvs_plan_pair",
+    "lvs_result_sum", "lvs_plan_pair", "lvs_ctx_max_launch_jobs", "lvs_ctx_set_max_launch_jobs",
     "lvs_decrypt", "lvs_decrypt_all", "lvs_pbs_batch_device", "lvs_keyswitch_batch_device",
     "lvs_poly_mul_device", "lvs_ctx_set_timing", "lvs_ctx_kernel_stats", "lvs_ctx_pbs_count",
     "lvs_ctx_launch_count", "lvs_ct_string_upload", "lvs_pbs_batch_device_noalloc",
@@ -158,6 +158,8 @@ def _declare(L):
         "lvs_ctx_br_split": ([vp, ctypes.POINTER(sz)], i32),
         "lvs_ctx_ks_gemm_min": ([vp, ctypes.POINTER(sz)], i32),
         "lvs_ctx_set_ks_gemm_min": ([vp, sz], i32),
+        "lvs_ctx_max_launch_jobs": ([vp, ctypes.POINTER(sz)], i32),
+        "lvs_ctx_set_max_launch_jobs": ([vp, sz], i32),
         "lvs_ctx_set_br_split": ([vp, sz], i32),
         "lvs_preprocess_batch": ([vp, vpp, sz, ctypes.c_char_p, sz, vpp], i32),
         "lvs_probe_int_mul": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
@@ -609,6 +611,16 @@ def lvs_ctx_ks_gemm_min(ctx):
 
 def lvs_ctx_set_ks_gemm_min(ctx, min_jobs):
     _check(lib().lvs_ctx_set_ks_gemm_min(ctx, min_jobs))
+
+
+def lvs_ctx_max_launch_jobs(ctx):
+    v = ctypes.c_size_t()
+    _check(lib().lvs_ctx_max_launch_jobs(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def lvs_ctx_set_max_launch_jobs(ctx, max_jobs):
+    _check(lib().lvs_ctx_set_max_launch_jobs(ctx, max_jobs))
 
 
 def lvs_ctx_br_split(ctx):

@@ -130,3 +130,31 @@ def test_refresh_full_parameters_long_pair():
     assert d == [P.wf_distance(a, b)]
     assert npbs == 2 * len(a) * len(b) + _refreshed_cells(len(a), len(b), set(diags))
     L.lvs_ctx_free(ctx)
+
+
+def test_split_launches_keep_refreshed_cells_together(small):
+    """Steps split over launches of at most `cap` PBS, the split falling at
+    many offsets of each step's job list: ciphertexts bit-exact with whole
+    steps, distances equal to Wagner-Fischer, the same PBS count.  The two
+    LUT_V lookups of a refreshed cell share a launch (the second reads the v
+    row the first one writes)."""
+    ck, ctx, K = small
+    pairs = [("kitten!", "sitting"), ("abcd", "dcbaab"), ("flaw", "lawns")]
+    r0, d0, n0 = _run(ck, ctx, pairs, P.ALPHA_ASCII7, 71, 25)
+    assert d0 == [P.wf_distance(a, b) for a, b in pairs]
+    base = [L.lvs_result_export(r0, k, K.big_dim) for k in range(len(pairs))]
+    launches = []
+    for cap in (2, 3, 5, 7):
+        L.lvs_ctx_set_max_launch_jobs(ctx, cap)
+        assert L.lvs_ctx_max_launch_jobs(ctx) == cap
+        l0 = L.lvs_ctx_launch_count(ctx)
+        r, d, n = _run(ck, ctx, pairs, P.ALPHA_ASCII7, 71, 25)
+        launches.append(L.lvs_ctx_launch_count(ctx) - l0)
+        assert n == n0 and d == d0, cap
+        for k in range(len(pairs)):
+            assert np.array_equal(L.lvs_result_export(r, k, K.big_dim), base[k]), (cap, k)
+    L.lvs_ctx_set_max_launch_jobs(ctx, 0)
+    assert L.lvs_ctx_max_launch_jobs(ctx) == 65536
+    assert launches[0] > launches[-1]
+    with pytest.raises(L.LvsError):
+        L.lvs_ctx_set_max_launch_jobs(ctx, 1)
