@@ -142,3 +142,20 @@ def test_null_arguments_are_rejected_before_any_device_work():
         assert call() == L.LVS_ERR_ARG, name
         assert lib.lvs_last_error().decode(), name
         assert out.value is None
+
+
+@pytest.mark.parametrize("field,value", [("k", 2), ("N", 1024), ("n", 0), ("n", 5000), ("pbs_level", 1),
+                                         ("pbs_level", 3), ("pbs_base_log", 14), ("ks_level", 9),
+                                         ("ks_level", 0), ("ks_base_log", 7), ("lwe_noise_log2", 61)])
+def test_parameter_limits(field, value):
+    """Parameter sets outside what the kernels implement (k = 1, N in {512,
+    2048}, a two-level bootstrapping gadget of <= 26 bits for three 30-bit NTT
+    primes, a key-switching gadget of <= 8 levels and <= 30 bits) are refused
+    on the host with LVS_ERR_ARG, by keygen and by the noise calls."""
+    p = L.lvs_params_default()
+    setattr(p, field, value)
+    with pytest.raises(L.LvsError) as e:
+        L.lvs_keygen(p, 0)
+    assert e.value.status == L.LVS_ERR_ARG
+    with pytest.raises(L.LvsError):
+        L.lvs_noise_budget(p, -64)
