@@ -267,6 +267,31 @@ Job make_job(const uint64_t *s0, int c0, const uint64_t *s1, int c1, const uint6
              uint8_t lut, uint8_t kind, uint64_t *d0, uint64_t *d1);
 lvs_status make_result(lvs_ctx *ctx, size_t rows, lvs_result **out);
 lvs_status finish_result(lvs_ctx *ctx, lvs_result *r);
+// Jobs of step `step` of the Section 5 table build of one encrypted string of m
+// characters against subset symbols sym (their two plaintext halves).  Two
+// lookups (C = 2): step 0 EQ1[r][i] = PBS(x1_i - sigma1_r; LUT_EQ), step 1
+// T[r][i] = PBS(2 (x2_i - sigma2_r) + 1 - EQ1[r][i]; LUT_EQ9).  DNA (C = 1):
+// step 0 T[r][i] = PBS(x_i - sigma_r; LUT_EQ9).  X(i, s) is the row of symbol s
+// of character i (from 0), E1(r, i) and T(r, i) the rows of EQ1 and of the table.
+template <class FX, class FE, class FT>
+void table_step_jobs(int step, uint32_t C, size_t m, const std::vector<std::pair<uint32_t, uint32_t>> &sym, FX X,
+                     FE E1, FT T, std::vector<Job> &jobs)
+{
+    for (size_t r = 0; r < sym.size(); ++r)
+        for (size_t i = 0; i < m; ++i) {
+            if (C == 1) {
+                if (step == 0)
+                    jobs.push_back(make_job(X(i, 0), 1, nullptr, 0, nullptr, 0, -(int)sym[r].first, LUT_EQ9, JOB_STORE,
+                                            T(r, i), nullptr));
+            } else if (step == 0) {
+                jobs.push_back(make_job(X(i, 0), 1, nullptr, 0, nullptr, 0, -(int)sym[r].first, LUT_EQ, JOB_STORE,
+                                        E1(r, i), nullptr));
+            } else {
+                jobs.push_back(make_job(X(i, 1), 2, E1(r, i), -1, nullptr, 0, 1 - 2 * (int)sym[r].second, LUT_EQ9,
+                                        JOB_STORE, T(r, i), nullptr));
+            }
+        }
+}
 // jobs of wavefront step s of one pair (cells of anti-diagonal s - depth, etc.)
 void plan_pair_step(const PairRows &P, const Arena &A, long s, std::vector<Job> &jobs);
 // number of steps of one pair (0 if it has no cell)

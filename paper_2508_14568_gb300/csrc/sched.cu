@@ -445,21 +445,11 @@ lvs_status lvs_preprocess_batch(lvs_ctx *ctx, const lvs_ct_string *const *encs, 
     for (int step = 0; step < 2; ++step) {
         for (size_t k = 0; k < count; ++k) {
             lvs_eq_table *t = tabs[k];
-            const size_t m = encs[k]->len, C = encs[k]->symbols, R = t->subset.size(), b0 = base[k];
-            auto T = [&](size_t r, size_t i) { return t->d + (r * m + i) * t->stride; };
-            for (size_t r = 0; r < R; ++r)
-                for (size_t i = 0; i < m; ++i) {
-                    if (C == 2 && step == 0)
-                        jobs.push_back(make_job(A.row(b0 + i * C), 1, nullptr, 0, nullptr, 0, -(int)syms[k][r].first,
-                                                LUT_EQ, JOB_STORE, A.row(b0 + m * C + r * m + i), nullptr));
-                    else if (C == 2)
-                        jobs.push_back(make_job(A.row(b0 + i * C + 1), 2, A.row(b0 + m * C + r * m + i), -1, nullptr,
-                                                0, 1 - 2 * (int)syms[k][r].second, LUT_EQ9, JOB_STORE, T(r, i),
-                                                nullptr));
-                    else if (step == 0)
-                        jobs.push_back(make_job(A.row(b0 + i), 1, nullptr, 0, nullptr, 0, -(int)syms[k][r].first,
-                                                LUT_EQ9, JOB_STORE, T(r, i), nullptr));
-                }
+            const size_t m = encs[k]->len, C = encs[k]->symbols, b0 = base[k];
+            table_step_jobs(
+                step, (uint32_t)C, m, syms[k], [&](size_t i, int s) { return A.row(b0 + i * C + s); },
+                [&](size_t r, size_t i) { return A.row(b0 + m * C + r * m + i); },
+                [&](size_t r, size_t i) { return t->d + (r * m + i) * t->stride; }, jobs);
         }
         off.push_back(jobs.size());
     }

@@ -120,22 +120,11 @@ void plan_query(const Query &q, std::vector<Job> &jobs)
 {
     if (q.step < q.prologue) {
         // preprocessing table of the reference symbols (Section 5)
-        const size_t R = q.subset.size(), m = q.m;
-        for (size_t rr = 0; rr < R; ++rr)
-            for (size_t i = 0; i < m; ++i) {
-                const uint64_t *x0 = q.A.row(q.P.x + i * q.C);
-                uint64_t *t = q.A.row(q.table + rr * m + i);
-                if (q.C == 1) {
-                    jobs.push_back(make_job(x0, 1, nullptr, 0, nullptr, 0, -(int)q.sym[rr].first, LUT_EQ9, JOB_STORE, t,
-                                            nullptr));
-                } else if (q.step == 0) {
-                    jobs.push_back(make_job(x0, 1, nullptr, 0, nullptr, 0, -(int)q.sym[rr].first, LUT_EQ, JOB_STORE,
-                                            q.A.row(q.tmp + rr * m + i), nullptr));
-                } else {
-                    jobs.push_back(make_job(q.A.row(q.P.x + i * q.C + 1), 2, q.A.row(q.tmp + rr * m + i), -1, nullptr, 0,
-                                            1 - 2 * (int)q.sym[rr].second, LUT_EQ9, JOB_STORE, t, nullptr));
-                }
-            }
+        const size_t m = q.m;
+        table_step_jobs(
+            (int)q.step, q.C, m, q.sym, [&](size_t i, int s) { return q.A.row(q.P.x + i * q.C + s); },
+            [&](size_t r, size_t i) { return q.A.row(q.tmp + r * m + i); },
+            [&](size_t r, size_t i) { return q.A.row(q.table + r * m + i); }, jobs);
         return;
     }
     plan_pair_step(q.P, q.A, q.step - q.prologue, jobs);
