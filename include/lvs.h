@@ -250,6 +250,15 @@ typedef struct lvs_plan_job {
 lvs_status lvs_plan_pair(size_t m, size_t n, uint32_t eq_lookups, int32_t band, const uint8_t *refresh,
                          const uint8_t *plain, const uint8_t *subset, size_t nsub, lvs_plan_layout *layout,
                          lvs_plan_job *jobs, size_t *count);
+/* The plan of the Section 5 table build of one encrypted string of m
+ * characters of `alphabet` against the nsub plaintext symbols of subset, as
+ * lvs_preprocess and the server build it (host only, no GPU).  Rows: [a: m*C]
+ * [EQ1 scratch: nsub*m, C = 2 only][table: nsub*m], T[k][i] at
+ * table + k*m + i - 1; layout.eq1 and layout.table give the blocks (v, h,
+ * path, eq9 and b are -1).  Jobs, count and errors as lvs_plan_pair; a subset
+ * symbol outside the alphabet or repeated gives LVS_ERR_ARG. */
+lvs_status lvs_plan_table(size_t m, lvs_alphabet alphabet, const uint8_t *subset, size_t nsub,
+                          lvs_plan_layout *layout, lvs_plan_job *jobs, size_t *count);
 
 /* Encrypted equality of characters a[i] and b[j] (Algorithm alg_ascii: 2 PBS
  * for ASCII7 / 27 symbols; Section 4.1: 1 PBS for DNA4).  times9 != 0 gives

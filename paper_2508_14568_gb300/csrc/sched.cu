@@ -481,6 +481,29 @@ void lvs_eq_table_free(lvs_eq_table *t)
     delete t;
 }
 
+// plan jobs -> exported rows (offsets from the base of a one-word-per-row array)
+static void export_jobs(const std::vector<Job> &J, const std::vector<int64_t> &step_of, const uint64_t *base,
+                        lvs_plan_job *jobs)
+{
+    auto row = [&](const uint64_t *q) -> int64_t { return q ? (int64_t)(q - base) : -1; };
+    for (size_t k = 0; k < J.size(); ++k) {
+        lvs_plan_job &o = jobs[k];
+        o.step = step_of[k];
+        for (int t = 0; t < 3; ++t) {
+            o.src[t] = row(J[k].src[t]);
+            o.coef[t] = J[k].src[t] ? J[k].coef[t] : 0;
+        }
+        o.cst = J[k].cst;
+        o.dst[0] = row(J[k].dst[0]);
+        o.dst[1] = row(J[k].dst[1]);
+        o.tap = J[k].tapsel ? row(J[k].tap) : -1;
+        o.lut = J[k].lut;
+        o.kind = J[k].kind;
+        o.tapsel = J[k].tapsel;
+        o.pad = 0;
+    }
+}
+
 lvs_status lvs_plan_pair(size_t m, size_t n, uint32_t eq_lookups, int32_t band, const uint8_t *refresh,
                          const uint8_t *plain, const uint8_t *subset, size_t nsub, lvs_plan_layout *layout,
                          lvs_plan_job *jobs, size_t *count)
@@ -551,23 +574,52 @@ lvs_status lvs_plan_pair(size_t m, size_t n, uint32_t eq_lookups, int32_t band, 
     *count = J.size();
     if (!jobs) return LVS_OK;
     if (room < J.size()) return set_error(LVS_ERR_ARG, "lvs_plan_pair: jobs has too little room");
-    auto row = [&](const uint64_t *q) -> int64_t { return q ? (int64_t)(q - A.d) : -1; };
-    for (size_t k = 0; k < J.size(); ++k) {
-        lvs_plan_job &o = jobs[k];
-        o.step = step_of[k];
-        for (int t = 0; t < 3; ++t) {
-            o.src[t] = row(J[k].src[t]);
-            o.coef[t] = J[k].src[t] ? J[k].coef[t] : 0;
-        }
-        o.cst = J[k].cst;
-        o.dst[0] = row(J[k].dst[0]);
-        o.dst[1] = row(J[k].dst[1]);
-        o.tap = J[k].tapsel ? row(J[k].tap) : -1;
-        o.lut = J[k].lut;
-        o.kind = J[k].kind;
-        o.tapsel = J[k].tapsel;
-        o.pad = 0;
+    export_jobs(J, step_of, A.d, jobs);
+    return LVS_OK;
+}
+
+lvs_status lvs_plan_table(size_t m, lvs_alphabet alphabet, const uint8_t *subset, size_t nsub,
+                          lvs_plan_layout *layout, lvs_plan_job *jobs, size_t *count)
+{
+    if (!count || (nsub && !subset)) return set_error(LVS_ERR_ARG, "lvs_plan_table: NULL argument");
+    const uint32_t C = symbols_per_char(alphabet);
+    if (alphabet_size(alphabet) == 0) return set_error(LVS_ERR_ARG, "lvs_plan_table: unknown alphabet");
+    std::vector<std::pair<uint32_t, uint32_t>> sym(nsub);
+    bool seen[256] = {};
+    for (size_t r = 0; r < nsub; ++r) {
+        uint32_t v[2] = {0, 0};
+        if (!encode_char(alphabet, subset[r], v) || seen[subset[r]])
+            return set_error(LVS_ERR_ARG, "lvs_plan_table: subset symbol outside the alphabet or repeated");
+        seen[subset[r]] = true;
+        sym[r] = {v[0], v[1]};
     }
+    lvs_plan_layout L;
+    L.a = 0;
+    L.b = L.v = L.h = L.path = L.eq9 = -1;
+    size_t r = m * C;
+    L.eq1 = C == 2 ? (int64_t)r : -1;
+    if (C == 2) r += nsub * m;
+    L.table = (int64_t)r;
+    r += nsub * m;
+    L.rows = (int64_t)r;
+    L.steps = (m && nsub) ? (int64_t)C : 0;
+    std::vector<uint64_t> base(r + 1);
+    uint64_t *b0 = base.data();
+    std::vector<Job> J;
+    std::vector<int64_t> step_of;
+    for (int st = 0; st < (int)L.steps; ++st) {
+        table_step_jobs(
+            st, C, m, sym, [&](size_t i, int s) { return b0 + i * C + s; },
+            [&](size_t k, size_t i) { return b0 + L.eq1 + k * m + i; },
+            [&](size_t k, size_t i) { return b0 + L.table + k * m + i; }, J);
+        step_of.resize(J.size(), st);
+    }
+    if (layout) *layout = L;
+    const size_t room = *count;
+    *count = J.size();
+    if (!jobs) return LVS_OK;
+    if (room < J.size()) return set_error(LVS_ERR_ARG, "lvs_plan_table: jobs has too little room");
+    export_jobs(J, step_of, b0, jobs);
     return LVS_OK;
 }
 

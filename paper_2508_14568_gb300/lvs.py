@@ -31,7 +31,7 @@ EXPORTS = [
     "lvs_ct_string_export", "lvs_ct_string_import", "lvs_decrypt_lwe", "lvs_encrypt_lwe", "lvs_eq",
     "lvs_edit_distance_batch", "lvs_preprocess", "lvs_eq_table_free",
     "lvs_edit_distance_preprocessed_batch", "lvs_result_info", "lvs_result_export", "lvs_result_free",
-    "lvs_result_sum", "lvs_plan_pair", "lvs_ctx_max_launch_jobs", "lvs_ctx_set_max_launch_jobs",
+    "lvs_result_sum", "lvs_plan_pair", "lvs_plan_table", "lvs_ctx_max_launch_jobs", "lvs_ctx_set_max_launch_jobs",
     "lvs_decrypt", "lvs_decrypt_all", "lvs_pbs_batch_device", "lvs_keyswitch_batch_device",
     "lvs_poly_mul_device", "lvs_ctx_set_timing", "lvs_ctx_kernel_stats", "lvs_ctx_pbs_count",
     "lvs_ctx_launch_count", "lvs_ct_string_upload", "lvs_pbs_batch_device_noalloc",
@@ -171,6 +171,8 @@ def _declare(L):
                             ctypes.POINTER(ctypes.c_double)], i32),
         "lvs_plan_pair": ([sz, sz, u32, i32, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, sz,
                            ctypes.POINTER(lvs_plan_layout), ctypes.POINTER(lvs_plan_job), szp], i32),
+        "lvs_plan_table": ([sz, i32, ctypes.c_char_p, sz, ctypes.POINTER(lvs_plan_layout),
+                            ctypes.POINTER(lvs_plan_job), szp], i32),
         "lvs_keyswitch_batch_device": ([vp, vp, sz, vp, sz], i32),
         "lvs_poly_mul_device": ([vp, vp, vp, vp, sz], i32),
         "lvs_ctx_set_timing": ([vp, i32], i32),
@@ -321,9 +323,23 @@ def lvs_plan_pair(m, n, eq_lookups, band=-1, refresh=None, plain=None, subset=No
     _check(lib().lvs_plan_pair(*args, None, ctypes.byref(cnt)))
     jobs = (lvs_plan_job * max(1, cnt.value))()
     _check(lib().lvs_plan_pair(*args, jobs, ctypes.byref(cnt)))
-    out = [{"step": j.step, "src": list(j.src), "coef": list(j.coef), "cst": j.cst, "dst": list(j.dst),
-            "tap": j.tap, "lut": j.lut, "kind": j.kind, "tapsel": j.tapsel} for j in jobs[:cnt.value]]
-    return lay.as_dict(), out
+    return lay.as_dict(), _plan_jobs(jobs, cnt.value)
+
+
+def _plan_jobs(jobs, n):
+    return [{"step": j.step, "src": list(j.src), "coef": list(j.coef), "cst": j.cst, "dst": list(j.dst),
+             "tap": j.tap, "lut": j.lut, "kind": j.kind, "tapsel": j.tapsel} for j in jobs[:n]]
+
+
+def lvs_plan_table(m, alphabet, subset):
+    """(layout dict, list of job dicts) of a Section 5 table build (host only)."""
+    sb = _bytes(subset)
+    lay = lvs_plan_layout()
+    cnt = ctypes.c_size_t(0)
+    _check(lib().lvs_plan_table(m, alphabet, sb, len(sb), ctypes.byref(lay), None, ctypes.byref(cnt)))
+    jobs = (lvs_plan_job * max(1, cnt.value))()
+    _check(lib().lvs_plan_table(m, alphabet, sb, len(sb), ctypes.byref(lay), jobs, ctypes.byref(cnt)))
+    return lay.as_dict(), _plan_jobs(jobs, cnt.value)
 
 
 def lvs_version():

@@ -41,9 +41,19 @@ def simulate(a, b, alphabet, band=-1, refresh=None, preprocessed=False):
     if lay["path"] >= 0:
         for r in range(lay["path"], lay["path"] + m + n):
             rows[r] = 1
+    _execute(rows, jobs, lay["steps"])
+    if lay["path"] >= 0:
+        dist = sum(P.signed(rows[lay["path"] + t]) for t in range(m + n))
+    else:
+        dist = m + sum(P.signed(rows[lay["h"] + t]) for t in range(n))
+    return dist, lay, jobs
+
+
+def _execute(rows, jobs, nsteps):
+    """Runs planned launch steps on the plaintext rows (in place)."""
     steps = sorted({j["step"] for j in jobs})
     assert steps == list(range(len(steps)))
-    assert len(steps) == lay["steps"]
+    assert len(steps) == nsteps
     for s in steps:
         step_jobs = [j for j in jobs if j["step"] == s]
         # key switch of the launch: every input is gathered before any output
@@ -78,11 +88,6 @@ def simulate(a, b, alphabet, band=-1, refresh=None, preprocessed=False):
                     updates.append((j["tap"], out))
         for r, v in updates:
             rows[r] = v
-    if lay["path"] >= 0:
-        dist = sum(P.signed(rows[lay["path"] + t]) for t in range(m + n))
-    else:
-        dist = m + sum(P.signed(rows[lay["h"] + t]) for t in range(n))
-    return dist, lay, jobs
 
 
 def _e9(a, b):
@@ -171,3 +176,58 @@ def test_plan_argument_errors():
         L.lvs_plan_pair(2, 2, 0, -1, None, "AB", "A")          # symbol outside the subset
     with pytest.raises(L.LvsError):
         L.lvs_plan_pair(2, 2, 0, -1, None, "AB", "ABA")        # repeated subset symbol
+
+
+@pytest.mark.parametrize("alphabet,lib_alpha,symbols", [
+    (P.ALPHA_ASCII7, L.LVS_ALPHA_ASCII7, "".join(chr(c) for c in range(128))),
+    (P.ALPHA_27, L.LVS_ALPHA_27, "ABCDEFGHIJKLMNOPQRSTUVWXYZ "),
+    (P.ALPHA_DNA4, L.LVS_ALPHA_DNA4, "ACGT")])
+def test_table_plan_computes_eq9_table(alphabet, lib_alpha, symbols):
+    """Section 5's table build as lvs_preprocess and the server plan it, run on
+    plaintext values: T[sigma][i] = 9 EQ(a_i, sigma) for every symbol of the
+    alphabet (Table tab_pre's table), 2 lookups per entry (1 for DNA)."""
+    rng = random.Random(65)
+    a = "".join(rng.choice(symbols) for _ in range(12)) + symbols[:3]
+    m, C = len(a), ALPHA[alphabet]
+    lay, jobs = L.lvs_plan_table(m, lib_alpha, symbols)
+    assert len(jobs) == C * m * len(symbols) and lay["steps"] == C
+    rows = [None] * lay["rows"]
+    for ci, c in enumerate(a):
+        for si, v in enumerate(P.split_symbol(P.symbol_index(c, alphabet), alphabet)):
+            rows[lay["a"] + ci * C + si] = v
+    _execute(rows, jobs, lay["steps"])
+    want = P.preprocess_table(a, symbols, alphabet)
+    for k, sym in enumerate(symbols):
+        assert [rows[lay["table"] + k * m + i] for i in range(m)] == want[sym], sym
+        assert want[sym] == [9 if x == sym else 0 for x in a]
+
+
+def test_table_then_preprocessed_plan_computes_wf():
+    """A plaintext-reference query as the server runs it: the table of the
+    reference's symbols, then one cell lookup per cell reading it."""
+    rng = random.Random(66)
+    for _ in range(40):
+        a = "".join(rng.choice("ABCD Z") for _ in range(rng.randint(1, 10)))
+        b = "".join(rng.choice("ABZ ") for _ in range(rng.randint(1, 10)))
+        subset = "".join(sorted(set(b)))
+        m, n = len(a), len(b)
+        tl, tjobs = L.lvs_plan_table(m, L.LVS_ALPHA_27, subset)
+        trows = [None] * tl["rows"]
+        for ci, c in enumerate(a):
+            for si, v in enumerate(P.split_symbol(P.symbol_index(c, P.ALPHA_27), P.ALPHA_27)):
+                trows[tl["a"] + ci * 2 + si] = v
+        _execute(trows, tjobs, tl["steps"])
+        lay, jobs = L.lvs_plan_pair(m, n, 0, -1, None, b, subset)
+        rows = [None] * lay["rows"]
+        rows[lay["table"]:lay["table"] + len(subset) * m] = trows[tl["table"]:tl["table"] + len(subset) * m]
+        for r in range(lay["v"], lay["h"] + n):
+            rows[r] = 1
+        _execute(rows, jobs, lay["steps"])
+        assert m + sum(P.signed(rows[lay["h"] + t]) for t in range(n)) == P.wf_distance(a, b)
+
+
+def test_table_plan_argument_errors():
+    with pytest.raises(L.LvsError):
+        L.lvs_plan_table(3, L.LVS_ALPHA_27, "Ab")        # lowercase outside the alphabet
+    with pytest.raises(L.LvsError):
+        L.lvs_plan_table(3, L.LVS_ALPHA_DNA4, "ACA")     # repeated
