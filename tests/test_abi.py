@@ -159,3 +159,59 @@ def test_parameter_limits(field, value):
     assert e.value.status == L.LVS_ERR_ARG
     with pytest.raises(L.LvsError):
         L.lvs_noise_budget(p, -64)
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <stdlib.h>
+#include "lvs.h"
+
+int main(void)
+{
+    lvs_params p;
+    lvs_client_key *ck = NULL;
+    lvs_server_key *sk = NULL;
+    uint64_t ct[513];
+    uint32_t v = 99;
+    double budget = 0.0;
+    size_t count = 0;
+    lvs_plan_layout lay;
+    lvs_ctx *ctx = NULL;
+    lvs_params_test(&p);
+    if (lvs_keygen(&p, 7, &ck, &sk) != LVS_OK) return 1;
+    for (uint32_t m = 0; m < 32; ++m) {
+        if (lvs_encrypt_lwe(ck, m, 3, 0, m, ct) != LVS_OK) return 2;
+        if (lvs_decrypt_lwe(ck, ct, &v) != LVS_OK || v != m) return 3;
+    }
+    lvs_params_default(&p);
+    if (lvs_noise_budget(&p, -64.0, &budget) != LVS_OK || budget < 80000.0 || budget > 95000.0) return 4;
+    if (lvs_plan_pair(4, 4, 2, -1, NULL, NULL, NULL, 0, &lay, NULL, &count) != LVS_OK || count != 48) return 5;
+    if (lvs_keygen(NULL, 0, &ck, &sk) != LVS_ERR_ARG || lvs_last_error()[0] == 0) return 6;
+    printf("%s\n", lvs_version());
+    lvs_client_key_free(ck);
+    lvs_server_key_free(sk);
+    lvs_ctx_free(ctx);                       /* NULL is accepted */
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_the_abi_links(tmp_path):
+    """include/lvs.h compiles as C99 (no C++ in the public interface), and a C
+    program linked against liblvs.so runs the host-side calls: keys, LWE
+    encryption round trip (Table tab_pbs's 48 PBS for a 4 x 4 ASCII pair in the
+    exported plan), the noise budget, error reporting."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    L.lib()                                   # builds liblvs.so if needed
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(L.LIB_PATH)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                           str(src), "-o", str(exe), "-L", libdir, "-llvs", "-Wl,-rpath," + libdir])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert "sm_103a" in out.stdout
