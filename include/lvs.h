@@ -112,6 +112,16 @@ lvs_status lvs_client_key_export(const lvs_client_key *ck, uint64_t *lwe_key, si
 lvs_status lvs_server_key_export(const lvs_server_key *sk, uint64_t *bsk, size_t *bsk_words,
                                  uint64_t *ksk, size_t *ksk_words);
 lvs_status lvs_server_key_params(const lvs_server_key *sk, lvs_params *out);
+/* Rebuild keys from exported material (the layouts above) for the parameter
+ * set params: how a server loads the evaluation keys a client sent it
+ * (Section 1's client / server setting), and how a client reloads its secret
+ * key.  The words are copied.  LVS_ERR_ARG for a NULL pointer, invalid
+ * params, word counts that do not match params, or (client key) a key
+ * coefficient other than 0 or 1. */
+lvs_status lvs_server_key_import(const lvs_params *params, const uint64_t *bsk, size_t bsk_words,
+                                 const uint64_t *ksk, size_t ksk_words, lvs_server_key **out);
+lvs_status lvs_client_key_import(const lvs_params *params, const uint64_t *lwe_key, size_t lwe_words,
+                                 const uint64_t *glwe_key, size_t glwe_words, lvs_client_key **out);
 
 /* ---------------------------------------------------------------- context */
 

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cstring>
 #include <functional>
+#include <new>
 #include <thread>
 
 #include "lvs_internal.hpp"
@@ -294,6 +295,53 @@ lvs_status lvs_server_key_export(const lvs_server_key *sk, uint64_t *bsk, size_t
     lvs_status st = export_vec(sk->bsk, bsk, bsk_words);
     if (st != LVS_OK) return st;
     return export_vec(sk->ksk, ksk, ksk_words);
+}
+
+lvs_status lvs_server_key_import(const lvs_params *params, const uint64_t *bsk, size_t bsk_words,
+                                 const uint64_t *ksk, size_t ksk_words, lvs_server_key **out)
+{
+    if (!params || !bsk || !ksk || !out) return set_error(LVS_ERR_ARG, "lvs_server_key_import: NULL argument");
+    lvs_status st = check_params(*params);
+    if (st != LVS_OK) return st;
+    Params P;
+    P.p = *params;
+    if (bsk_words != P.bsk_words() || ksk_words != P.ksk_words())
+        return set_error(LVS_ERR_ARG, "lvs_server_key_import: key sizes do not match the parameters");
+    lvs_server_key *sk = new (std::nothrow) lvs_server_key;
+    if (!sk) return set_error(LVS_ERR_OOM, "lvs_server_key_import: host allocation failed");
+    try {
+        sk->P = P;
+        sk->bsk.assign(bsk, bsk + bsk_words);
+        sk->ksk.assign(ksk, ksk + ksk_words);
+    } catch (const std::bad_alloc &) {
+        delete sk;
+        return set_error(LVS_ERR_OOM, "lvs_server_key_import: host allocation failed");
+    }
+    *out = sk;
+    return LVS_OK;
+}
+
+lvs_status lvs_client_key_import(const lvs_params *params, const uint64_t *lwe_key, size_t lwe_words,
+                                 const uint64_t *glwe_key, size_t glwe_words, lvs_client_key **out)
+{
+    if (!params || !lwe_key || !glwe_key || !out) return set_error(LVS_ERR_ARG, "lvs_client_key_import: NULL argument");
+    lvs_status st = check_params(*params);
+    if (st != LVS_OK) return st;
+    Params P;
+    P.p = *params;
+    if (lwe_words != P.p.n || glwe_words != P.big())
+        return set_error(LVS_ERR_ARG, "lvs_client_key_import: key sizes do not match the parameters");
+    for (size_t i = 0; i < lwe_words; ++i)
+        if (lwe_key[i] > 1) return set_error(LVS_ERR_ARG, "lvs_client_key_import: LWE key is not binary");
+    for (size_t i = 0; i < glwe_words; ++i)
+        if (glwe_key[i] > 1) return set_error(LVS_ERR_ARG, "lvs_client_key_import: GLWE key is not binary");
+    lvs_client_key *ck = new (std::nothrow) lvs_client_key;
+    if (!ck) return set_error(LVS_ERR_OOM, "lvs_client_key_import: host allocation failed");
+    ck->P = P;
+    ck->lwe_key.assign(lwe_key, lwe_key + lwe_words);
+    ck->glwe_key.assign(glwe_key, glwe_key + glwe_words);
+    *out = ck;
+    return LVS_OK;
 }
 
 lvs_status lvs_server_key_params(const lvs_server_key *sk, lvs_params *out)

@@ -26,7 +26,8 @@ STATUS_NAMES = ["LVS_OK", "LVS_ERR_ARG", "LVS_ERR_OOM", "LVS_ERR_CUDA", "LVS_ERR
 EXPORTS = [
     "lvs_last_error", "lvs_version", "lvs_params_default", "lvs_params_test", "lvs_opts_default",
     "lvs_keygen", "lvs_client_key_free", "lvs_server_key_free", "lvs_client_key_export",
-    "lvs_server_key_export", "lvs_server_key_params", "lvs_ctx_create", "lvs_ctx_free",
+    "lvs_server_key_export", "lvs_server_key_params", "lvs_server_key_import", "lvs_client_key_import",
+    "lvs_ctx_create", "lvs_ctx_free",
     "lvs_ctx_synchronize", "lvs_encrypt_string", "lvs_ct_string_free", "lvs_ct_string_info",
     "lvs_ct_string_export", "lvs_ct_string_import", "lvs_decrypt_lwe", "lvs_encrypt_lwe", "lvs_eq",
     "lvs_edit_distance_batch", "lvs_preprocess", "lvs_eq_table_free",
@@ -126,6 +127,8 @@ def _declare(L):
         "lvs_server_key_free": ([vp], None),
         "lvs_client_key_export": ([vp, u64p, szp, u64p, szp], i32),
         "lvs_server_key_export": ([vp, u64p, szp, u64p, szp], i32),
+        "lvs_server_key_import": ([ctypes.POINTER(lvs_params), u64p, sz, u64p, sz, vpp], i32),
+        "lvs_client_key_import": ([ctypes.POINTER(lvs_params), u64p, sz, u64p, sz, vpp], i32),
         "lvs_server_key_params": ([vp, P], i32),
         "lvs_ctx_create": ([vp, i32, vp, vpp], i32),
         "lvs_ctx_free": ([vp], None),
@@ -368,6 +371,24 @@ def lvs_server_key_export(sk):
     bsk, ksk = np.zeros(a.value, np.uint64), np.zeros(b.value, np.uint64)
     _check(lib().lvs_server_key_export(sk, _u64p(bsk), ctypes.byref(a), _u64p(ksk), ctypes.byref(b)))
     return bsk, ksk
+
+
+def lvs_server_key_import(params, bsk, ksk):
+    bsk = np.ascontiguousarray(bsk, np.uint64)
+    ksk = np.ascontiguousarray(ksk, np.uint64)
+    out = ctypes.c_void_p()
+    _check(lib().lvs_server_key_import(ctypes.byref(params), _u64p(bsk), bsk.size, _u64p(ksk), ksk.size,
+                                       ctypes.byref(out)))
+    return ServerKey(out.value)
+
+
+def lvs_client_key_import(params, lwe_key, glwe_key):
+    lwe_key = np.ascontiguousarray(lwe_key, np.uint64)
+    glwe_key = np.ascontiguousarray(glwe_key, np.uint64)
+    out = ctypes.c_void_p()
+    _check(lib().lvs_client_key_import(ctypes.byref(params), _u64p(lwe_key), lwe_key.size, _u64p(glwe_key),
+                                       glwe_key.size, ctypes.byref(out)))
+    return ClientKey(out.value)
 
 
 def lvs_server_key_params(sk):

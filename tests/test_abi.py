@@ -215,3 +215,32 @@ def test_header_is_plain_c_and_the_abi_links(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, (out.returncode, out.stderr)
     assert "sm_103a" in out.stdout
+
+
+def test_key_import_round_trip():
+    """Keys rebuilt from their exported words (a server loading the client's
+    evaluation keys) export the same words; the imported client key decrypts
+    what the original encrypted, and mismatched or non-binary material is
+    refused."""
+    p = L.lvs_params_test()
+    ck, sk = L.lvs_keygen(p, 11)
+    lwe, glwe = L.lvs_client_key_export(ck)
+    bsk, ksk = L.lvs_server_key_export(sk)
+    sk2 = L.lvs_server_key_import(p, bsk, ksk)
+    b2, k2 = L.lvs_server_key_export(sk2)
+    assert np.array_equal(b2, bsk) and np.array_equal(k2, ksk)
+    assert L.lvs_server_key_params(sk2).as_dict() == p.as_dict()
+    ck2 = L.lvs_client_key_import(p, lwe, glwe)
+    s = L.lvs_encrypt_string(ck, "Hello", L.LVS_ALPHA_ASCII7, 5, 0)
+    s2 = L.lvs_encrypt_string(ck2, "Hello", L.LVS_ALPHA_ASCII7, 5, 0)
+    assert np.array_equal(L.lvs_ct_string_export(s), L.lvs_ct_string_export(s2))
+    for row in L.lvs_ct_string_export(s).reshape(-1, p.N + 1):
+        assert L.lvs_decrypt_lwe(ck2, row) == L.lvs_decrypt_lwe(ck, row)
+    with pytest.raises(L.LvsError):
+        L.lvs_server_key_import(p, bsk[:-1], ksk)
+    with pytest.raises(L.LvsError):
+        L.lvs_server_key_import(L.lvs_params_default(), bsk, ksk)
+    bad = glwe.copy()
+    bad[3] = 2
+    with pytest.raises(L.LvsError):
+        L.lvs_client_key_import(p, lwe, bad)
