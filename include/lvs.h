@@ -344,6 +344,13 @@ lvs_status lvs_result_sum(lvs_ctx *ctx, const lvs_result *r, lvs_result **out);
 lvs_status lvs_decrypt(const lvs_client_key *ck, const lvs_result *r, size_t pair, uint32_t *dist);
 /* Decrypts every item of a result; dist has room for `items` values. */
 lvs_status lvs_decrypt_all(const lvs_client_key *ck, const lvs_result *r, uint32_t *dist);
+/* Client side, for a result received as exported words (lvs_result_export on
+ * the server, lvs_result_info for m and n): the distance base + the sum of
+ * the `count` rows ([count][k*N+1]) decoded to {-1, 0, 1}, with base = m for
+ * the last row h[m][1..n] (count = n) and 0 for a band path (count = m + n);
+ * a summed result (lvs_result_sum) is one row with base 0.  Host only. */
+lvs_status lvs_decrypt_distance(const lvs_client_key *ck, const uint64_t *rows, size_t count, int64_t base,
+                                uint32_t *dist);
 
 /* ---------------------------------------------------------------- serving */
 

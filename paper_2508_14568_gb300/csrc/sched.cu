@@ -812,6 +812,20 @@ lvs_status lvs_decrypt(const lvs_client_key *ck, const lvs_result *r, size_t pai
     return decrypt_rows(ck, r, host.data(), pair, dist);
 }
 
+lvs_status lvs_decrypt_distance(const lvs_client_key *ck, const uint64_t *rows, size_t count, int64_t base,
+                                uint32_t *dist)
+{
+    if (!ck || !dist || (count && !rows)) return set_error(LVS_ERR_ARG, "lvs_decrypt_distance: NULL argument");
+    const size_t w = (size_t)ck->P.big() + 1;
+    long d = (long)base;
+    for (size_t j = 0; j < count; ++j) {
+        const uint32_t v = decrypt_lwe(*ck, rows + j * w);
+        d += v >= 16 ? (long)v - 32 : (long)v;
+    }
+    *dist = (uint32_t)std::max(0L, d);
+    return LVS_OK;
+}
+
 lvs_status lvs_decrypt_all(const lvs_client_key *ck, const lvs_result *r, uint32_t *dist)
 {
     if (!ck || !r || (!dist && !r->items.empty())) return set_error(LVS_ERR_ARG, "lvs_decrypt_all: NULL argument");

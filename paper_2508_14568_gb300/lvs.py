@@ -27,6 +27,7 @@ EXPORTS = [
     "lvs_last_error", "lvs_version", "lvs_params_default", "lvs_params_test", "lvs_opts_default",
     "lvs_keygen", "lvs_client_key_free", "lvs_server_key_free", "lvs_client_key_export",
     "lvs_server_key_export", "lvs_server_key_params", "lvs_server_key_import", "lvs_client_key_import",
+    "lvs_decrypt_distance",
     "lvs_ctx_create", "lvs_ctx_free",
     "lvs_ctx_synchronize", "lvs_encrypt_string", "lvs_ct_string_free", "lvs_ct_string_info",
     "lvs_ct_string_export", "lvs_ct_string_import", "lvs_decrypt_lwe", "lvs_encrypt_lwe", "lvs_eq",
@@ -152,6 +153,7 @@ def _declare(L):
         "lvs_result_sum": ([vp, vp, vpp], i32),
         "lvs_decrypt": ([vp, vp, sz, u32p], i32),
         "lvs_decrypt_all": ([vp, vp, u32p], i32),
+        "lvs_decrypt_distance": ([vp, u64p, sz, ctypes.c_int64, u32p], i32),
         "lvs_pbs_batch_device": ([vp, vp, sz, vp, vp, sz, sz], i32),
         "lvs_pbs_batch_device_fft64": ([vp, vp, sz, vp, vp, sz, sz], i32),
         "lvs_ctx_prepare_fft64": ([vp, vp], i32),
@@ -569,6 +571,15 @@ def lvs_decrypt(ck, r, pair):
     v = ctypes.c_uint32()
     _check(lib().lvs_decrypt(ck, r, pair, ctypes.byref(v)))
     return v.value
+
+
+def lvs_decrypt_distance(ck, rows, base):
+    """Distance from exported result rows ([count][k*N+1]) and the base."""
+    rows = np.ascontiguousarray(rows, np.uint64)
+    count = rows.shape[0] if rows.ndim == 2 else 0
+    d = ctypes.c_uint32()
+    _check(lib().lvs_decrypt_distance(ck, _u64p(rows), count, int(base), ctypes.byref(d)))
+    return d.value
 
 
 def lvs_decrypt_all(ck, r):

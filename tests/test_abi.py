@@ -244,3 +244,19 @@ def test_key_import_round_trip():
     bad[3] = 2
     with pytest.raises(L.LvsError):
         L.lvs_client_key_import(p, lwe, bad)
+
+
+def test_decrypt_distance_from_exported_rows():
+    """The client's readout (Algorithm algo_complete's m + sum of the last row)
+    from rows received as words: differences -1 / 0 / 1 as Z_32 residues."""
+    p = L.lvs_params_test()
+    ck, _ = L.lvs_keygen(p, 12)
+    K = T.Keys(T.params_test(), 12)
+    a, b = "kitten", "sitting"
+    _, h, _, _ = P.lvs_plain(a, b)
+    m, n = len(a), len(b)
+    rows = np.stack([T.encrypt(K, h[m][j], 4, 0, j) for j in range(1, n + 1)])
+    assert L.lvs_decrypt_distance(ck, rows, m) == P.wf_distance(a, b) == 3
+    assert L.lvs_decrypt_distance(ck, np.zeros((0, p.N + 1), np.uint64), 5) == 5
+    one = np.stack([T.encrypt(K, 3, 4, 1, 0)])
+    assert L.lvs_decrypt_distance(ck, one, 0) == 3           # a summed result
