@@ -160,7 +160,7 @@ struct lvs_ctx {
     lvs::KsPlan ks_tuned[lvs::kKsBuckets];   // autotuned plans (tj = 0: default heuristic)
     lvs::KsGemm *ks_gemm = nullptr;  // key switch as bf16 GEMMs (null: unavailable)
     size_t ks_gemm_min = 0;          // launches of at least this many PBS use it (0: never)
-    size_t max_launch_jobs = 0;      // wider wavefront steps run as several launches
+    size_t max_launch_jobs = (size_t)1 << 16;   // wider wavefront steps run as several launches
     uint64_t pbs_done = 0;
     uint64_t launches = 0;
     lvs::Timing timing;
