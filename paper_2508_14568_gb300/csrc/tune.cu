@@ -206,6 +206,7 @@ lvs_status lvs_ctx_set_ks_gemm_min(lvs_ctx *ctx, size_t min_jobs)
     if (!ctx) return set_error(LVS_ERR_ARG, "lvs_ctx_set_ks_gemm_min: NULL context");
     if (min_jobs > 0 && !ctx->ks_gemm)
         return set_error(LVS_ERR_STATE, "lvs_ctx_set_ks_gemm_min: the tensor-core key switch is unavailable");
+    std::lock_guard<std::mutex> lock(ctx->mu);   // batch calls read it under the lock
     ctx->ks_gemm_min = min_jobs;
     return LVS_OK;
 }
@@ -240,6 +241,7 @@ lvs_status lvs_ctx_set_br_split(lvs_ctx *ctx, size_t max_jobs)
     if (!ctx) return set_error(LVS_ERR_ARG, "lvs_ctx_set_br_split: NULL context");
     if (max_jobs > 0 && ctx->br_clusters <= 0)
         return set_error(LVS_ERR_STATE, "lvs_ctx_set_br_split: the device cannot run the three-CTA form");
+    std::lock_guard<std::mutex> lock(ctx->mu);
     ctx->br_split_max = max_jobs;
     return LVS_OK;
 }
@@ -252,6 +254,7 @@ lvs_status lvs_ctx_set_ks_plan(lvs_ctx *ctx, size_t njobs, int32_t jobs_per_cta,
     KsPlan pl;
     pl.tj = jobs_per_cta;
     pl.split = jobs_per_cta ? split : 1;
+    std::lock_guard<std::mutex> lock(ctx->mu);
     ctx->ks_tuned[ks_bucket(njobs)] = pl;
     return LVS_OK;
 }
