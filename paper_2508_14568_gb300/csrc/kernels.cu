@@ -41,30 +41,43 @@ __device__ __forceinline__ uint64_t test_poly_at(const uint8_t (&f)[16], uint32_
     return neg ? 0 - v : v;
 }
 
-// External product core for prime group g: digit residues d (L0 layout, in
-// [0, p)) -> forward NTT -> Montgomery products with the key slice `key`
-// ([16][T][8] u32 for this prime, this thread at +tau*8) -> inverse NTT ->
-// residues of the two output polynomials written to out[j*N + e].
-template <int LOGN>
-__device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][16], const uint32_t *__restrict__ key,
-                                                 uint32_t *buf, uint32_t *out, uint32_t tau, int g,
-                                                 const uint2 *__restrict__ twf, const uint2 *__restrict__ twi)
+// Read-only load of key data that bypasses L1 (each key word is used once per
+// CMux; L1 keeps the twiddles instead).
+__device__ __forceinline__ uint4 ld_key(const uint4 *p)
 {
-    using Lay = Layout<LOGN>;
-    constexpr int N = Lay::N, T = Lay::T;
-    const uint32_t p = c_pc.p[g], pinv = c_pc.pinv_neg[g];
-    ntt_forward4<LOGN>(d, reinterpret_cast<uint4 *>(buf), tau, twf, p, 1 + g);
+    uint4 r;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p));
+    return r;
+}
 
-    // pointwise: out_c = sum_r D_r * K[r][c] (Montgomery), written over D_0, D_1
+// External product core for prime group g: digit residues d (pass-0 layout,
+// in [0, 2p)) -> forward NTT -> Montgomery products with the key slice `key`
+// ([8][T][8] u32 for this prime, this thread at +tau*8) -> inverse NTT ->
+// residues of the two output polynomials written to out[j*N + e].
+template <int L>
+__device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][8], const uint32_t *__restrict__ key,
+                                                 uint32_t *buf, uint32_t *out, uint32_t tau, int g,
+                                                 const uint2 *__restrict__ twf, const uint2 *__restrict__ twi,
+                                                 int bar_id)
+{
+    using G = Geo<L>;
+    constexpr int N = G::N, T = G::T;
+    const uint32_t p = c_pc.p[g], pinv = c_pc.pinv_neg[g];
+    ntt_forward4<L>(d, reinterpret_cast<uint4 *>(buf), tau, twf, p, bar_id);
+
+    // pointwise in the last layout (e = tau << 3 | q): out_c = sum_r D_r * K[r][c]
+    // (Montgomery), written over D_0, D_1
     const uint4 *kp = reinterpret_cast<const uint4 *>(key + (size_t)tau * 8);
-    uint4 ka = __ldg(kp), kb = __ldg(kp + 1);
+    uint4 ka = ld_key(kp), kb = ld_key(kp + 1);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
+    for (int q = 0; q < 8; ++q) {
         uint4 na, nb;
-        if (q + 1 < 16) {
+        if (q + 1 < 8) {
             const uint4 *np = kp + (size_t)(q + 1) * T * 2;
-            na = __ldg(np);
-            nb = __ldg(np + 1);
+            na = ld_key(np);
+            nb = ld_key(np + 1);
         }
         // transform values in [0, 4p) -> [0, 2p); key residues < p: each sum of
         // four products is below 8 p^2 < 2^63, REDC returns it below 3p, and one
@@ -78,36 +91,35 @@ __device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][16], const uin
         const uint64_t t1 = (uint64_t)d0 * ka.y + (uint64_t)d1 * ka.w + (uint64_t)d2 * kb.y + (uint64_t)d3 * kb.w;
         d[0][q] = csub(redc(t0, p, pinv), 2 * p);
         d[1][q] = csub(redc(t1, p, pinv), 2 * p);
-        if (q + 1 < 16) { ka = na; kb = nb; }
+        if (q + 1 < 8) { ka = na; kb = nb; }
     }
-    ntt_inverse2<LOGN>(d, reinterpret_cast<uint2 *>(buf), tau, twi, p, 1 + g);
+    ntt_inverse2<L>(d, reinterpret_cast<uint2 *>(buf), tau, twi, p, bar_id);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        const uint32_t e = tau | ((uint32_t)q << Lay::B0);
+    for (int q = 0; q < 8; ++q) {
+        const uint32_t e = tau | ((uint32_t)q << (L - 3));
         out[0 * N + e] = csub(d[0][q], p);
         out[1 * N + e] = csub(d[1][q], p);
     }
 }
 
-// Digit residues (mod this group's prime) of X^a ACC - ACC at the 16 positions
-// of the thread in the L0 layout, for the mask (j = 0) and body (j = 1)
-// polynomials of the negacyclically extended accumulator acc ([2][2N]).
-// Only the rounded top 2*base_log bits of x are used: with
-// shift = 64 - 2*base_log >= 32, (x + 2^(shift-1)) >> shift =
-// (hi32(x) + 2^(shift-33)) >> (shift-32).  Balanced digits with carry,
-// least significant level first; d < 0 is stored as d + p (< 2p is fine).
-template <int LOGN>
-__device__ __forceinline__ void decompose(uint32_t (&d)[4][16], const uint64_t *acc, uint32_t a, uint32_t tau,
+// Digit residues (mod this group's prime) of X^a ACC - ACC at the 8 positions
+// of the thread in the pass-0 layout (e = q << (L-3) | tau), for the mask
+// (j = 0) and body (j = 1) polynomials of the negacyclically extended
+// accumulator acc ([2][2N]).  Only the rounded top 2*base_log bits of x are
+// used: with shift = 64 - 2*base_log >= 32, (x + 2^(shift-1)) >> shift =
+// (hi32(x) + 2^(shift-33)) >> (shift-32).  Balanced digits with carry, least
+// significant level first; d < 0 is stored as d + p (<= p).
+template <int L>
+__device__ __forceinline__ void decompose(uint32_t (&d)[4][8], const uint64_t *acc, uint32_t a, uint32_t tau,
                                           uint32_t base_log, uint32_t pmB)
 {
-    using Lay = Layout<LOGN>;
-    constexpr int N = Lay::N;
+    constexpr int N = 1 << L;
     const uint32_t B = 1u << base_log, hB = B >> 1;
     const uint32_t hshift = 64 - 2 * base_log - 32;   // shift - 32
     const uint32_t hround = 1u << (hshift - 1);       // 2^(shift - 33)
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        const uint32_t e = tau | ((uint32_t)q << Lay::B0);
+    for (int q = 0; q < 8; ++q) {
+        const uint32_t e = tau | ((uint32_t)q << (L - 3));
         const uint32_t src = (e - a) & (2 * N - 1);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -150,6 +162,9 @@ __device__ __forceinline__ void sample_extract_epilogue(const Job &J, const uint
 }
 
 // ---------------------------------------------------------------- blind rotation
+// One CTA per ciphertext: three prime groups of T = N/8 threads (768 threads
+// at N = 2048), each group running its prime's transforms; the CRT and the
+// accumulator update are spread over the whole CTA.
 template <int LOGN>
 struct BrSmem {
     static constexpr int N = 1 << LOGN;
@@ -160,13 +175,13 @@ struct BrSmem {
 };
 
 template <int LOGN>
-__global__ void __launch_bounds__(3 * (1 << LOGN) / 16, 1)
+__global__ void __launch_bounds__(3 * (1 << LOGN) / 8, 1)
 k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__restrict__ ms, uint32_t n, const uint32_t *__restrict__ bsk,
                const uint2 *__restrict__ tw, const uint8_t *__restrict__ luts, int lut_per_job,
                uint32_t base_log)
 {
-    using Lay = Layout<LOGN>;
-    constexpr int N = Lay::N, T = Lay::T, NT = 3 * T;
+    using G = Geo<LOGN>;
+    constexpr int N = G::N, T = G::T, NT = 3 * T;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint64_t *acc = reinterpret_cast<uint64_t *>(smem_raw);
     uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw + BrSmem<LOGN>::acc_bytes);
@@ -180,7 +195,7 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
     const uint2 *twf = tw + (size_t)(g * 2 + 0) * N;
     const uint2 *twi = tw + (size_t)(g * 2 + 1) * N;
     const uint32_t pmB = p - (1u << base_log);
-    const size_t key_row = (size_t)3 * 16 * T * 8;   // u32 per BSK index i
+    const size_t key_row = (size_t)3 * 8 * T * 8;   // u32 per BSK index i
 
     for (uint32_t job = blockIdx.x; job < njobs; job += gridDim.x) {
         const Job J = jobs[job];
@@ -203,10 +218,10 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
         for (uint32_t i = 0; i < n; ++i) {
             const uint32_t a = __ldg(msj + i);
             if (a == 0) continue;   // X^0 ACC - ACC = 0: the external product is exactly 0
-            uint32_t d[4][16];
+            uint32_t d[4][8];
             decompose<LOGN>(d, acc, a, tau, base_log, pmB);
-            ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 16 * T * 8, buf, crt + g * 2 * N, tau,
-                                   g, twf, twi);
+            ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 8 * T * 8, buf, crt + g * 2 * N, tau,
+                                   g, twf, twi, 1 + g);
             __syncthreads();
             for (int c = tid; c < 2 * N; c += NT) {
                 const int j = c >> LOGN, e = c & (N - 1);
@@ -379,15 +394,17 @@ __global__ void k_ksk_colsum(const uint64_t *__restrict__ ksk, uint32_t rows, ui
 
 // ---------------------------------------------------------------- key conversion
 // BSK (coefficient domain, [i][row][col][N] u64) -> NTT domain
-// out[i][g][q][tau][slot = row*2+col] = NTT_p(row,col)[pos(tau,q)] * R * N^{-1} mod p
+// out[i][g][q][tau][slot = row*2+col] = NTT_p(row,col)[tau << 3 | q] * R * N^{-1} mod p
+// (the last-layout position of register q of thread tau: the order in which
+// the blind rotation's threads hold the transformed digits)
 template <int LOGN>
-__global__ void __launch_bounds__(3 * (1 << LOGN) / 16)
+__global__ void __launch_bounds__(3 * (1 << LOGN) / 8)
 k_bsk_to_ntt(const uint64_t *__restrict__ coef, uint32_t count, uint32_t *__restrict__ out,
              const uint2 *__restrict__ tw, uint32_t m0, uint32_t ms0, uint32_t m1, uint32_t ms1, uint32_t m2,
              uint32_t ms2)
 {
-    using Lay = Layout<LOGN>;
-    constexpr int N = Lay::N, T = Lay::T;
+    using G = Geo<LOGN>;
+    constexpr int N = G::N, T = G::T;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw);
     const int tid = threadIdx.x, g = tid / T;
@@ -395,22 +412,22 @@ k_bsk_to_ntt(const uint64_t *__restrict__ coef, uint32_t count, uint32_t *__rest
     const uint32_t i = blockIdx.x, h = blockIdx.y;   // h: slots 4h..4h+3
     if (i >= count) return;
     const uint32_t p = c_pc.p[g];
-    uint32_t v[4][16];
+    uint32_t v[4][8];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const uint32_t slot = 4 * h + k;   // = row * 2 + col
         const uint64_t *src = coef + ((size_t)i * 8 + slot) * N;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const uint32_t e = tau | ((uint32_t)q << Lay::B0);
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t e = tau | ((uint32_t)q << (LOGN - 3));
             v[k][q] = residue_of_signed((int64_t)src[e], p);
         }
     }
     ntt_forward4<LOGN>(v, reinterpret_cast<uint4 *>(bufs + g * 4 * N), tau, tw + (size_t)(g * 2) * N, p, 1 + g);
     const uint32_t m = g == 0 ? m0 : (g == 1 ? m1 : m2), msh = g == 0 ? ms0 : (g == 1 ? ms1 : ms2);
-    uint32_t *dst = out + (size_t)i * 3 * 16 * T * 8 + (size_t)g * 16 * T * 8 + (size_t)tau * 8 + 4 * h;
+    uint32_t *dst = out + (size_t)i * 3 * 8 * T * 8 + (size_t)g * 8 * T * 8 + (size_t)tau * 8 + 4 * h;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
+    for (int q = 0; q < 8; ++q) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const uint32_t x = csub(csub(v[k][q], 2 * p), p);
@@ -440,14 +457,14 @@ struct BrClSmem {
 };
 
 template <int LOGN>
-__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__((1 << LOGN) / 16, 2)
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__((1 << LOGN) / 8, 2)
 k_blind_rotate_cl(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__restrict__ ms, uint32_t n,
                   const uint32_t *__restrict__ bsk, const uint2 *__restrict__ tw, const uint8_t *__restrict__ luts,
                   int lut_per_job, uint32_t base_log)
 {
     namespace cg = cooperative_groups;
-    using Lay = Layout<LOGN>;
-    constexpr int N = Lay::N, T = Lay::T;
+    using G = Geo<LOGN>;
+    constexpr int N = G::N, T = G::T;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint64_t *acc = reinterpret_cast<uint64_t *>(smem_raw);
@@ -460,7 +477,7 @@ k_blind_rotate_cl(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *
     const uint2 *twf = tw + (size_t)(g * 2 + 0) * N;
     const uint2 *twi = tw + (size_t)(g * 2 + 1) * N;
     const uint32_t pmB = p - (1u << base_log);
-    const size_t key_row = (size_t)3 * 16 * T * 8;
+    const size_t key_row = (size_t)3 * 8 * T * 8;
     const uint32_t *res_of[3];
     uint64_t *acc_of[3];
 #pragma unroll
@@ -488,10 +505,10 @@ k_blind_rotate_cl(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *
         for (uint32_t i = 0; i < n; ++i) {
             const uint32_t a = __ldg(msj + i);
             if (a == 0) continue;   // the same for the three CTAs
-            uint32_t d[4][16];
+            uint32_t d[4][8];
             decompose<LOGN>(d, acc, a, tau, base_log, pmB);
-            ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 16 * T * 8, buf, res, tau, g, twf,
-                                   twi);
+            ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 8 * T * 8, buf, res, tau, g, twf,
+                                   twi, 1);
             cl.sync();   // the three primes' residues are in place
             for (int c = g * T + (int)tau; c < 2 * N; c += 3 * T) {
                 const int j = c >> LOGN, e = c & (N - 1);
@@ -512,12 +529,12 @@ k_blind_rotate_cl(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *
 
 // Product-only kernel (parity of the NTT/CRT path): out[item] = sum_r dig[r] * key[r][col]
 template <int LOGN>
-__global__ void __launch_bounds__(3 * (1 << LOGN) / 16, 1)
+__global__ void __launch_bounds__(3 * (1 << LOGN) / 8, 1)
 k_poly_mul(const int32_t *__restrict__ dig, const uint32_t *__restrict__ keyntt, uint64_t *__restrict__ out,
            uint32_t count, const uint2 *__restrict__ tw)
 {
-    using Lay = Layout<LOGN>;
-    constexpr int N = Lay::N, T = Lay::T, NT = 3 * T;
+    using G = Geo<LOGN>;
+    constexpr int N = G::N, T = G::T, NT = 3 * T;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw + BrSmem<LOGN>::acc_bytes);
     uint32_t *crt = bufs + 3 * 4 * N;
@@ -526,18 +543,18 @@ k_poly_mul(const int32_t *__restrict__ dig, const uint32_t *__restrict__ keyntt,
     const uint32_t item = blockIdx.x;
     if (item >= count) return;
     const uint32_t p = c_pc.p[g];
-    uint32_t d[4][16];
+    uint32_t d[4][8];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const uint32_t e = tau | ((uint32_t)q << Lay::B0);
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t e = tau | ((uint32_t)q << (LOGN - 3));
             const int32_t x = dig[((size_t)item * 4 + r) * N + e];
             d[r][q] = x < 0 ? (uint32_t)(x + (int32_t)p) : (uint32_t)x;
         }
-    ext_product_core<LOGN>(d, keyntt + (size_t)item * 3 * 16 * T * 8 + (size_t)g * 16 * T * 8,
+    ext_product_core<LOGN>(d, keyntt + (size_t)item * 3 * 8 * T * 8 + (size_t)g * 8 * T * 8,
                            bufs + g * 4 * N, crt + g * 2 * N, tau, g, tw + (size_t)(g * 2) * N,
-                           tw + (size_t)(g * 2 + 1) * N);
+                           tw + (size_t)(g * 2 + 1) * N, 1 + g);
     __syncthreads();
     for (int c = tid; c < 2 * N; c += NT) {
         const int j = c >> LOGN, e = c & (N - 1);
@@ -561,9 +578,9 @@ __global__ void k_fill_trivial(uint64_t *arena, size_t stride, uint32_t big, siz
 // ---------------------------------------------------------------- host wrappers
 using namespace dev;
 
-int br_threads(uint32_t N) { return 3 * (int)N / 16; }
+int br_threads(uint32_t N) { return 3 * (int)N / 8; }
 int br_smem_bytes(uint32_t N) { return N == 2048 ? (int)BrSmem<11>::total : (int)BrSmem<9>::total; }
-size_t bsk_ntt_words(uint32_t n, uint32_t N) { return (size_t)n * 3 * 16 * (N / 16) * 8; }
+size_t bsk_ntt_words(uint32_t n, uint32_t N) { return (size_t)n * 3 * 8 * (N / 8) * 8; }
 
 cudaError_t upload_prime_consts(const PrimeConsts &pc) { return cudaMemcpyToSymbol(c_pc, &pc, sizeof(pc)); }
 
@@ -588,7 +605,7 @@ static int max_clusters()
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(3, 1, 1);
-    cfg.blockDim = dim3((1 << LOGN) / 16, 1, 1);
+    cfg.blockDim = dim3((1 << LOGN) / 8, 1, 1);
     cfg.dynamicSmemBytes = BrClSmem<LOGN>::total;
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeClusterDimension;
@@ -702,10 +719,10 @@ cudaError_t launch_blind_rotate(const lvs_ctx *ctx, const Job *jobs, size_t njob
         // small launch: one ciphertext per cluster of three CTAs (one per prime)
         const unsigned grid = 3 * (unsigned)std::min<size_t>(njobs, (size_t)ctx->br_clusters);
         if (p.N == 2048)
-            k_blind_rotate_cl<11><<<grid, (1 << 11) / 16, BrClSmem<11>::total, s>>>(
+            k_blind_rotate_cl<11><<<grid, (1 << 11) / 8, BrClSmem<11>::total, s>>>(
                 jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log);
         else
-            k_blind_rotate_cl<9><<<grid, (1 << 9) / 16, BrClSmem<9>::total, s>>>(
+            k_blind_rotate_cl<9><<<grid, (1 << 9) / 8, BrClSmem<9>::total, s>>>(
                 jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log);
         return cudaGetLastError();
     }
