@@ -64,6 +64,11 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="config 5: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="config 5: arrival window in seconds")
     ap.add_argument("--slots", type=int, default=16, help="config 5: server slots (admitted queries)")
+    ap.add_argument("--serve-rate", type=float, default=2.0,
+                    help="serving segment of the default run: Poisson arrivals per second (0: no segment)")
+    ap.add_argument("--serve-duration", type=float, default=30.0, help="serving segment: arrival window in seconds")
+    ap.add_argument("--serve-alone", type=int, default=16,
+                    help="serving segment: queries of the segment also run one at a time (alone on the server)")
     ap.add_argument("--serial-pairs", type=int, default=8,
                     help="pairs run one at a time for the one-pair-at-a-time comparison (0: skip)")
     ap.add_argument("--pairs", type=int, default=None, help="override the number of pairs (small profiling cases)")
@@ -477,6 +482,12 @@ def run_lvs(args):
                "note": "pinned host encrypted strings -> lvs_edit_distance_batch (H2D inside) -> D2H + client "
                        "decryption"}
 
+    # serving segment: continuous batching at a sustainable rate, with the same
+    # queries one at a time (rank 0, N = 1; not part of value)
+    serving = None
+    if rank == 0 and world == 1 and cfg == 2 and args.serve_rate > 0:
+        serving = serving_segment(L, ctx, ck, args.serve_rate, args.serve_duration, args.slots, args.serve_alone)
+
     # CPU oracle baseline (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -489,15 +500,21 @@ def run_lvs(args):
         d_in = torch.from_numpy(np.ascontiguousarray(cts).view(np.int64)).cuda()
         d_lut = torch.from_numpy(np.ascontiguousarray(luts.astype(np.uint8))).cuda()
         d_out = torch.zeros_like(d_in)
-        # the oracle keys equal the library keys from the same seed
+        # the oracle keys equal the library keys from the same seed; the sample
+        # runs through the blind-rotation form of the timed launches (one CTA
+        # per ciphertext), not the three-CTA form its small size would pick
+        split0 = L.lvs_ctx_br_split(ctx)
+        L.lvs_ctx_set_br_split(ctx, 0)
         L.lvs_pbs_batch_device(ctx, d_in, big + 1, d_lut, d_out, big + 1, count)
         L.lvs_ctx_synchronize(ctx)
+        L.lvs_ctx_set_br_split(ctx, split0)
         same = bool(np.array_equal(d_out.cpu().numpy().view(np.uint64), out))
         pbs_s = count / dt
         cpu = {"value": pbs_s / pbs_per_cell(cfg), "unit": "cells/s", "cores": cores, "kind": "oracle",
                "sample": "%d full-parameter PBS of the workload on %d threads (%.1f s); cells/s = PBS/s / %d"
                          % (count, cores, dt, pbs_per_cell(cfg)),
-               "pbs_per_s": pbs_s, "sample_bit_exact_vs_gpu": same}
+               "pbs_per_s": pbs_s, "sample_bit_exact_vs_gpu": same,
+               "sample_gpu_form": "k_blind_rotate (one CTA per ciphertext), as in the timed launches"}
 
     if rank == 0:
         line = {
@@ -537,7 +554,9 @@ def run_lvs(args):
                         "br_three_cta_max_pbs": br_split,
                         "ks_tensor_core_min_pbs": ks_gemm_min},
             "latency_ms": {"p50": batched_latency_ms, "p99": batched_latency_ms,
-                           "note": "batched: all pairs of a step complete together"},
+                           "note": "the batch step time: all pairs of a step complete together (query "
+                                   "latencies under continuous batching: serving)"},
+            "serving": serving,
             "one_pair_at_a_time": serial,
             "table_build": table_build,
             "noise": noise,
@@ -552,6 +571,81 @@ def run_lvs(args):
     return 0
 
 
+def encrypt_arrivals(L, ck, arrivals, seed=5):
+    """Client side: every query (and encrypted reference) encrypted before the clock starts."""
+    enc = []
+    for k, (t, q, ref, plain) in enumerate(arrivals):
+        qa = L.lvs_encrypt_string(ck, q, L.LVS_ALPHA_27, seed, 2 * k)
+        rb = None if plain else L.lvs_encrypt_string(ck, ref, L.LVS_ALPHA_27, seed, 2 * k + 1)
+        enc.append((qa, rb))
+    return enc
+
+
+def serve(L, server, arrivals, enc, idx=None):
+    """Submits the queries `idx` (default: all) at their arrival times (seconds
+    after the call) and polls until every one is done; returns {i: latency s}
+    (completion - arrival) and {i: result}."""
+    idx = list(range(len(arrivals))) if idx is None else list(idx)
+    t0 = time.perf_counter()
+    tickets, done_t, results = {}, {}, {}
+    k = 0
+    while len(done_t) < len(idx):
+        now = time.perf_counter() - t0
+        while k < len(idx) and arrivals[idx[k]][0] <= now:
+            i = idx[k]
+            qa, rb = enc[i]
+            tickets[i] = L.lvs_server_submit(server, qa, ref_enc=rb) if rb is not None else \
+                L.lvs_server_submit(server, qa, ref_plain=arrivals[i][2])
+            k += 1
+        for i, tk in tickets.items():
+            if i not in done_t:
+                r = L.lvs_server_poll(server, tk)
+                if r is not None:
+                    done_t[i] = time.perf_counter() - t0
+                    results[i] = r
+        time.sleep(0.001)
+    return {i: done_t[i] - arrivals[i][0] for i in done_t}, results, time.perf_counter() - t0
+
+
+def pct(lat, q):
+    v = sorted(lat)
+    return 1e3 * v[min(len(v) - 1, int(q * len(v)))]
+
+
+def serving_segment(L, ctx, ck, rate, duration, slots, alone):
+    """Continuous batching at a sustainable rate (config 5's generator), and a
+    sample of the same queries run one at a time (each alone on the server:
+    the plain one-pair-at-a-time GPU form on the same inputs)."""
+    from paper_2508_14568_gb300 import workloads as W
+    arrivals = W.config5(rate=rate, duration=duration)
+    enc = encrypt_arrivals(L, ck, arrivals)
+    server = L.lvs_server_create(ctx, 64 << 30, slots)
+    lat, res, wall = serve(L, server, arrivals, enc)
+    st = L.lvs_server_stats_get(server)
+    ok = all(L.lvs_decrypt(ck, res[i], 0) == levenshtein(arrivals[i][1], arrivals[i][2]) for i in res)
+    cells = sum(len(q) * len(ref) for _, q, ref, _ in arrivals)
+    out = {"workload": "config 5 generator: Poisson %.1f queries/s for %.0f s, 27 symbols, lengths U[4,64], "
+                       "plaintext/encrypted reference 50/50, %d slots" % (rate, duration, slots),
+           "queries": len(arrivals), "latency_ms": {"p50": pct(lat.values(), 0.5), "p99": pct(lat.values(), 0.99),
+                                                    "max": 1e3 * max(lat.values())},
+           "cells_per_s": cells / wall, "pbs_per_s": st["pbs"] / wall, "gpu_busy_frac": st["busy_ms"] / 1e3 / wall,
+           "all_distances_correct": ok, "note": "latency = completion - arrival, wall clock"}
+    if alone > 0:
+        sample = list(range(0, len(arrivals), max(1, len(arrivals) // alone)))[:alone]
+        lat1 = []
+        ok1 = True
+        for i in sample:
+            one = [(0.0,) + tuple(arrivals[i][1:])]
+            l1, r1, _ = serve(L, server, one, [enc[i]])
+            lat1.append(l1[0])
+            ok1 &= L.lvs_decrypt(ck, r1[0], 0) == L.lvs_decrypt(ck, res[i], 0)
+        out["one_at_a_time"] = {"queries": len(sample), "latency_ms": {"p50": pct(lat1, 0.5), "p99": pct(lat1, 0.99)},
+                                "same_distances_as_in_the_mix": bool(ok1),
+                                "note": "the same queries submitted one at a time, each alone on the server"}
+    L.lvs_server_free(server)
+    return out
+
+
 def run_serving(args):
     """Config 5: Poisson arrivals of encrypted 27-symbol queries (length
     U[4,64]) against plaintext or encrypted references (U[4,64], 50/50) into the
@@ -563,46 +657,20 @@ def run_serving(args):
     params = L.lvs_params_default()
     ck, sk = L.lvs_keygen(params, 0)
     ctx = L.lvs_ctx_create(sk, 0)
-    # encrypt everything before the clock starts (client side)
-    enc = []
-    for k, (t, q, ref, plain) in enumerate(arrivals):
-        qa = L.lvs_encrypt_string(ck, q, L.LVS_ALPHA_27, 5, 2 * k)
-        rb = None if plain else L.lvs_encrypt_string(ck, ref, L.LVS_ALPHA_27, 5, 2 * k + 1)
-        enc.append((qa, rb))
+    enc = encrypt_arrivals(L, ck, arrivals)
     server = L.lvs_server_create(ctx, 64 << 30, args.slots)
     clocks = ClockSampler(0)
     clocks.start()
-    t0 = time.perf_counter()
-    tickets, submit_t, done_t, results = [], [], {}, {}
-    k = 0
-    while len(done_t) < len(arrivals):
-        now = time.perf_counter() - t0
-        while k < len(arrivals) and arrivals[k][0] <= now:
-            qa, rb = enc[k]
-            tk = L.lvs_server_submit(server, qa, ref_enc=rb) if rb is not None else \
-                L.lvs_server_submit(server, qa, ref_plain=arrivals[k][2])
-            tickets.append(tk)
-            submit_t.append(arrivals[k][0])
-            k += 1
-        for i, tk in enumerate(tickets):
-            if i not in done_t:
-                r = L.lvs_server_poll(server, tk)
-                if r is not None:
-                    done_t[i] = time.perf_counter() - t0
-                    results[i] = r
-        time.sleep(0.001)
-    wall = time.perf_counter() - t0
+    lat, results, wall = serve(L, server, arrivals, enc)
     clk = clocks.stop()
     st = L.lvs_server_stats_get(server)
-    lat = sorted(done_t[i] - submit_t[i] for i in done_t)
     ok = all(L.lvs_decrypt(ck, results[i], 0) == levenshtein(arrivals[i][1], arrivals[i][2]) for i in results)
     cells = sum(len(q) * len(ref) for _, q, ref, _ in arrivals)
     line = {"metric": "serving p50/p99 query latency", "config": {
                 "workload": "config 5: Poisson %.1f queries/s for %.0f s, 27 symbols, lengths U[4,64], "
                             "plaintext/encrypted reference 50/50, budget 64 GB, %d slots" % (args.rate, args.duration, args.slots),
                 "queries": len(arrivals)},
-            "latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                           "max": 1e3 * lat[-1]},
+            "latency_ms": {"p50": pct(lat.values(), 0.5), "p99": pct(lat.values(), 0.99), "max": 1e3 * max(lat.values())},
             "cells_per_s": cells / wall, "pbs_per_s": st["pbs"] / wall, "wall_s": wall,
             "server": st, "all_distances_correct": ok, "clocks": clk}
     print(json.dumps(line), flush=True)

@@ -129,7 +129,12 @@ lvs_status lvs_client_key_import(const lvs_params *params, const uint64_t *lwe_k
  * the bootstrapping key to the NTT domain (three 30-bit primes, in the
  * register order of the blind-rotation kernel) and sets up tables.  `stream`
  * is a cudaStream_t to run on (NULL = a new non-blocking stream owned by the
- * context).  Device memory: about 1.5x the BSK plus the KSK. */
+ * context).  Device memory: about 1.5x the BSK plus the KSK.
+ * Threads: a context may be shared by host threads.  Every call that uses its
+ * stream, scratch memory, launch settings, counters or timing state takes the
+ * context's lock for the whole call, so such calls (batch calls, the
+ * device-pointer calls below, the tuning setters and getters, timing,
+ * lvs_ctx_synchronize) run one at a time in the order the lock is taken. */
 lvs_status lvs_ctx_create(const lvs_server_key *sk, int device, void *stream, lvs_ctx **out);
 void lvs_ctx_free(lvs_ctx *ctx);
 lvs_status lvs_ctx_synchronize(lvs_ctx *ctx);
@@ -451,7 +456,11 @@ lvs_status lvs_pbs_batch_device_fft64(lvs_ctx *ctx, const uint64_t *d_in, size_t
  * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share the one array and every call rewrites
  * the part it uses before reading it (nothing needs to start at zero): calls
  * that overlap on the GPU -- different streams or contexts of the same device
- * -- race on it; issue them on one stream or serialise them. */
+ * -- race on it; issue them on one stream or serialise them.  The call holds
+ * the context's lock like the other calls on a context.  It launches three
+ * kernels (job descriptors, key switch, blind rotation; lvs_ctx_launch_count
+ * counts them) and, with timing on, records its key-switch and blind-rotation
+ * times only with the events lvs_ctx_set_timing created in advance. */
 #define LVS_NOALLOC_SCRATCH_BYTES (4u << 20)
 lvs_status lvs_pbs_batch_device_noalloc(lvs_ctx *ctx, const uint64_t *d_in, size_t in_stride,
                                         const uint8_t *d_lut, uint64_t *d_out, size_t out_stride,
@@ -484,9 +493,10 @@ lvs_status lvs_ctx_br_split(lvs_ctx *ctx, size_t *max_jobs);
 lvs_status lvs_ctx_set_br_split(lvs_ctx *ctx, size_t max_jobs);
 /* Key-switch launches of at least min_jobs PBS run as a dense product on the
  * tensor cores: digits (|d| <= 4) times the key-switching key split into its
- * eight bytes, bf16 x bf16 -> fp32 cuBLAS GEMMs over four chunks of the
- * reduction dimension (every partial sum an integer below 2^22, so exact),
- * recombined mod 2^64 -- the same result bit for bit.  Default 1024;
+ * eight bytes, one bf16 x bf16 -> fp32 product over the whole reduction
+ * (every partial sum an integer below 2^24 in magnitude, so exact) in the
+ * library's own kernel, which rebuilds the words mod 2^64 and
+ * modulus-switches them -- the same result bit for bit.  Default 1024;
  * lvs_ctx_autotune measures the crossover; 0 turns it off.  LVS_ERR_STATE if
  * the context could not set it up (it then uses the kernel for every size). */
 lvs_status lvs_ctx_ks_gemm_min(lvs_ctx *ctx, size_t *min_jobs);
@@ -527,7 +537,12 @@ lvs_status lvs_poly_mul_device(lvs_ctx *ctx, const int32_t *d_dig, const uint64_
                                uint64_t *d_out, size_t count);
 
 /* Kernel timing over a region of calls (CUDA events on the context stream).
- * kind: 0 = blind rotation kernel, 1 = key-switch kernel. */
+ * kind: 0 = blind rotation kernel, 1 = key-switch kernel.  Enabling creates a
+ * pool of events up front (calls take events from it and return them once the
+ * times are read); a call that finds the pool empty creates more, except the
+ * allocation-free entry point, which then leaves its launches untimed.  Batch
+ * calls stay on their CUDA graph while timing is on: the events are recorded
+ * by event-record nodes of the graph, so the timed launches are the graph's. */
 typedef struct lvs_kernel_stats {
     uint64_t launches;        /* kernel launches timed                          */
     uint64_t items;           /* PBS (or key switches) processed by them        */

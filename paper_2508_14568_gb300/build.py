@@ -64,10 +64,7 @@ def build(force=False, verbose=False):
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp%d" % os.getpid()
-    # cuBLAS (the key switch of large launches) from the toolkit next to nvcc
-    libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-L", libdir, "-Xlinker", "-rpath", "-Xlinker", libdir,
-                                                           "-lcublas", "-lpthread"]
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

@@ -67,7 +67,7 @@ lvs_status ensure_scratch(lvs_ctx *ctx, size_t njobs_total, size_t njobs_step)
     return LVS_OK;
 }
 
-static cudaEvent_t pool_event(lvs_ctx *ctx)
+cudaEvent_t pool_event(lvs_ctx *ctx)
 {
     if (!ctx->timing.pool.empty()) {
         cudaEvent_t e = ctx->timing.pool.back();
@@ -119,21 +119,29 @@ static void reap_graphs(lvs_ctx *ctx, bool wait)
     }
 }
 
-static lvs_status launch_step(lvs_ctx *ctx, const Job *d_jobs, size_t nj, bool timed)
+// One launch step: the key switch (with the a2 gather) and the blind rotation.
+// timed: CUDA events around both kernels; captured: the step is being
+// captured into a graph, where the events become event-record nodes (external
+// records) that the graph executes in place.
+static lvs_status launch_step(lvs_ctx *ctx, const Job *d_jobs, size_t nj, bool timed, bool captured)
 {
     nvtxMarkA(("lvs step: " + std::to_string(nj) + " PBS").c_str());
     cudaEvent_t a = nullptr, b = nullptr, c = nullptr;
+    auto rec = [&](cudaEvent_t e) {
+        return captured ? cudaEventRecordWithFlags(e, ctx->stream, cudaEventRecordExternal)
+                        : cudaEventRecord(e, ctx->stream);
+    };
     if (timed) {
         a = pool_event(ctx); b = pool_event(ctx); c = pool_event(ctx);
         if (!a || !b || !c) return set_error(LVS_ERR_CUDA, "event creation failed");
-        LVS_CUDA(cudaEventRecord(a, ctx->stream));
+        LVS_CUDA(rec(a));
     }
     int nks = 0;
     LVS_CUDA(launch_keyswitch_auto(ctx, d_jobs, nj, ctx->ms, ctx->stream, &nks));
-    if (timed) LVS_CUDA(cudaEventRecord(b, ctx->stream));
+    if (timed) LVS_CUDA(rec(b));
     LVS_CUDA(launch_blind_rotate(ctx, d_jobs, nj, ctx->ms, ctx->luts, 0, ctx->stream));
     if (timed) {
-        LVS_CUDA(cudaEventRecord(c, ctx->stream));
+        LVS_CUDA(rec(c));
         ctx->timing.pending.push_back({a, b, c, nj});
     }
     ctx->launches += nks + 1;
@@ -178,18 +186,26 @@ lvs_status run_steps(lvs_ctx *ctx, const std::vector<Job> &jobs, const std::vect
     LVS_CUDA(cudaMemcpyAsync(ctx->jobs, jobs.data(), jobs.size() * sizeof(Job), cudaMemcpyHostToDevice,
                              ctx->stream));
     const bool timed = ctx->timing.enabled;
-    // the tensor-core key switch goes through cuBLAS, which is not captured:
-    // runs with such a step launch directly
-    const bool gemm_step = ctx->ks_gemm && ctx->ks_gemm_min && widest >= ctx->ks_gemm_min;
     // graphs need a capturable stream (not the legacy default stream)
-    if (use_graph && !timed && !gemm_step && ctx->stream != nullptr && off.size() > 2) {
+    if (use_graph && ctx->stream != nullptr && off.size() > 2) {
+        if (timed) {
+            // every event the capture records exists before the capture starts
+            size_t nl = 0;
+            for (size_t s = 0; s + 1 < off.size(); ++s)
+                for (size_t c0 = off[s]; c0 < off[s + 1]; c0 = chunk_end(ctx, jobs, c0, off[s + 1])) ++nl;
+            while (ctx->timing.pool.size() < 3 * nl) {
+                cudaEvent_t e = nullptr;
+                if (cudaEventCreate(&e) != cudaSuccess) return set_error(LVS_ERR_CUDA, "event creation failed");
+                ctx->timing.pool.push_back(e);
+            }
+        }
         cudaGraph_t graph = nullptr;
         LVS_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
         lvs_status lst = LVS_OK;
         for (size_t s = 0; s + 1 < off.size() && lst == LVS_OK; ++s)
             for (size_t c0 = off[s], c1; c0 < off[s + 1] && lst == LVS_OK; c0 = c1) {
                 c1 = chunk_end(ctx, jobs, c0, off[s + 1]);
-                lst = launch_step(ctx, ctx->jobs + c0, c1 - c0, false);
+                lst = launch_step(ctx, ctx->jobs + c0, c1 - c0, timed, true);
             }
         cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
         if (lst != LVS_OK) { if (graph) cudaGraphDestroy(graph); return lst; }
@@ -208,7 +224,7 @@ lvs_status run_steps(lvs_ctx *ctx, const std::vector<Job> &jobs, const std::vect
         for (size_t s = 0; s + 1 < off.size(); ++s)
             for (size_t c0 = off[s], c1; c0 < off[s + 1]; c0 = c1) {
                 c1 = chunk_end(ctx, jobs, c0, off[s + 1]);
-                st = launch_step(ctx, ctx->jobs + c0, c1 - c0, timed);
+                st = launch_step(ctx, ctx->jobs + c0, c1 - c0, timed, false);
                 if (st != LVS_OK) return st;
             }
     }
@@ -322,6 +338,7 @@ void lvs_ctx_free(lvs_ctx *ctx)
 lvs_status lvs_ctx_synchronize(lvs_ctx *ctx)
 {
     if (!ctx) return set_error(LVS_ERR_ARG, "lvs_ctx_synchronize: NULL context");
+    std::lock_guard<std::mutex> lock(ctx->mu);
     LVS_CUDA(cudaSetDevice(ctx->device));
     LVS_CUDA(cudaStreamSynchronize(ctx->stream));
     reap_graphs(ctx, true);
@@ -331,11 +348,18 @@ lvs_status lvs_ctx_synchronize(lvs_ctx *ctx)
 lvs_status lvs_ctx_set_timing(lvs_ctx *ctx, int enable)
 {
     if (!ctx) return set_error(LVS_ERR_ARG, "lvs_ctx_set_timing: NULL context");
+    std::lock_guard<std::mutex> lock(ctx->mu);
     timing_collect(ctx);
     ctx->timing.enabled = enable != 0;
     if (enable) {
         ctx->timing.stats[0] = lvs_kernel_stats{};
         ctx->timing.stats[1] = lvs_kernel_stats{};
+        // events for the calls that create none themselves (the allocation-free entry point)
+        while (ctx->timing.pool.size() < kTimingPoolEvents) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) return set_error(LVS_ERR_CUDA, "lvs_ctx_set_timing: event creation failed");
+            ctx->timing.pool.push_back(e);
+        }
     }
     return LVS_OK;
 }
@@ -343,6 +367,7 @@ lvs_status lvs_ctx_set_timing(lvs_ctx *ctx, int enable)
 lvs_status lvs_ctx_kernel_stats(lvs_ctx *ctx, int kind, lvs_kernel_stats *out)
 {
     if (!ctx || !out || kind < 0 || kind > 1) return set_error(LVS_ERR_ARG, "lvs_ctx_kernel_stats: bad argument");
+    std::lock_guard<std::mutex> lock(ctx->mu);
     LVS_CUDA(cudaSetDevice(ctx->device));
     timing_collect(ctx);
     *out = ctx->timing.stats[kind];
@@ -352,6 +377,7 @@ lvs_status lvs_ctx_kernel_stats(lvs_ctx *ctx, int kind, lvs_kernel_stats *out)
 lvs_status lvs_ctx_pbs_count(lvs_ctx *ctx, uint64_t *out)
 {
     if (!ctx || !out) return set_error(LVS_ERR_ARG, "lvs_ctx_pbs_count: NULL argument");
+    std::lock_guard<std::mutex> lock(ctx->mu);
     *out = ctx->pbs_done;
     return LVS_OK;
 }
@@ -359,6 +385,7 @@ lvs_status lvs_ctx_pbs_count(lvs_ctx *ctx, uint64_t *out)
 lvs_status lvs_ctx_launch_count(lvs_ctx *ctx, uint64_t *out)
 {
     if (!ctx || !out) return set_error(LVS_ERR_ARG, "lvs_ctx_launch_count: NULL argument");
+    std::lock_guard<std::mutex> lock(ctx->mu);
     *out = ctx->launches;
     return LVS_OK;
 }
@@ -372,6 +399,7 @@ lvs_status lvs_pbs_batch_device(lvs_ctx *ctx, const uint64_t *d_in, size_t in_st
     if (in_stride < big + 1 || out_stride < big + 1)
         return set_error(LVS_ERR_ARG, "lvs_pbs_batch_device: stride smaller than k*N+1");
     if (count == 0) return LVS_OK;
+    std::lock_guard<std::mutex> lock(ctx->mu);
     LVS_CUDA(cudaSetDevice(ctx->device));
     const size_t chunk = 1u << 16;
     for (size_t c0 = 0; c0 < count; c0 += chunk) {
@@ -415,6 +443,7 @@ lvs_status lvs_keyswitch_batch_device(lvs_ctx *ctx, const uint64_t *d_in, size_t
     if (!ctx || (count && (!d_in || !d_out))) return set_error(LVS_ERR_ARG, "lvs_keyswitch_batch_device: NULL argument");
     if (in_stride < (size_t)ctx->P.big() + 1) return set_error(LVS_ERR_ARG, "lvs_keyswitch_batch_device: bad stride");
     if (count == 0) return LVS_OK;
+    std::lock_guard<std::mutex> lock(ctx->mu);
     LVS_CUDA(cudaSetDevice(ctx->device));
     std::vector<Job> jobs(count);
     for (size_t i = 0; i < count; ++i) {
@@ -436,6 +465,7 @@ lvs_status lvs_poly_mul_device(lvs_ctx *ctx, const int32_t *d_dig, const uint64_
 {
     if (!ctx || (count && (!d_dig || !d_poly || !d_out))) return set_error(LVS_ERR_ARG, "lvs_poly_mul_device: NULL argument");
     if (count == 0) return LVS_OK;
+    std::lock_guard<std::mutex> lock(ctx->mu);
     LVS_CUDA(cudaSetDevice(ctx->device));
     const uint32_t N = ctx->P.p.N;
     uint32_t *tmp = nullptr;

@@ -262,6 +262,7 @@ lvs_status lvs_ctx_prepare_fft64(lvs_ctx *ctx, const lvs_server_key *sk)
     const auto &p = ctx->P.p;
     if (memcmp(&sk->P.p, &p, sizeof(p)) != 0)
         return set_error(LVS_ERR_ARG, "lvs_ctx_prepare_fft64: server key parameters differ from the context's");
+    std::lock_guard<std::mutex> lock(ctx->mu);
     if (ctx->bsk_fft) return LVS_OK;
     LVS_CUDA(cudaSetDevice(ctx->device));
     const uint32_t N = p.N, M = N / 2, n = p.n;
@@ -311,6 +312,7 @@ lvs_status lvs_pbs_batch_device_fft64(lvs_ctx *ctx, const uint64_t *d_in, size_t
 {
     if (!ctx || (count && (!d_in || !d_lut || !d_out)))
         return set_error(LVS_ERR_ARG, "lvs_pbs_batch_device_fft64: NULL argument");
+    std::lock_guard<std::mutex> lock(ctx->mu);
     if (!ctx->bsk_fft)
         return set_error(LVS_ERR_STATE, "lvs_pbs_batch_device_fft64: call lvs_ctx_prepare_fft64 first");
     const auto &p = ctx->P.p;

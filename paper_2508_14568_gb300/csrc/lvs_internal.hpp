@@ -158,7 +158,7 @@ struct lvs_ctx {
     uint64_t *ks_part = nullptr;   // split key-switch partial sums
     size_t ks_part_cap = 0;        // words
     lvs::KsPlan ks_tuned[lvs::kKsBuckets];   // autotuned plans (tj = 0: default heuristic)
-    lvs::KsGemm *ks_gemm = nullptr;  // key switch as bf16 GEMMs (null: unavailable)
+    lvs::KsGemm *ks_gemm = nullptr;  // key switch on the tensor cores (null: unavailable)
     size_t ks_gemm_min = 0;          // launches of at least this many PBS use it (0: never)
     size_t max_launch_jobs = (size_t)1 << 16;   // wider wavefront steps run as several launches
     uint64_t pbs_done = 0;
@@ -309,4 +309,8 @@ lvs_status ensure_scratch(lvs_ctx *ctx, size_t njobs_total, size_t njobs_step);
 lvs_status run_steps(lvs_ctx *ctx, const std::vector<Job> &jobs, const std::vector<size_t> &step_off,
                      bool use_graph);
 void timing_collect(lvs_ctx *ctx);
+// a timing event from the context's pool (created if the pool is empty; null on failure)
+cudaEvent_t pool_event(lvs_ctx *ctx);
+// events created up front by lvs_ctx_set_timing(ctx, 1): one launch step uses three
+constexpr size_t kTimingPoolEvents = 48;
 }  // namespace lvs

@@ -83,6 +83,7 @@ extern "C" lvs_status lvs_pbs_batch_device_noalloc(lvs_ctx *ctx, const uint64_t 
                                           " per call for n = " + std::to_string(ctx->P.p.n) + ")");
     }
     if (count == 0) return LVS_OK;
+    std::lock_guard<std::mutex> lock(ctx->mu);   // the settings and counters the batch calls share
     LVS_CUDA(cudaSetDevice(ctx->device));
     unsigned char *base = nullptr;
     lvs_status st = scratch_address(ctx->device, &base);
@@ -92,9 +93,23 @@ extern "C" lvs_status lvs_pbs_batch_device_noalloc(lvs_ctx *ctx, const uint64_t 
     k_fill_raw_jobs<<<(unsigned)((count + 127) / 128), 128, 0, ctx->stream>>>(jobs, d_in, in_stride, d_out, out_stride,
                                                                             (uint32_t)count);
     LVS_CUDA(cudaGetLastError());
+    // timing (lvs_ctx_set_timing): only events the context created up front,
+    // so that this call creates nothing; with the pool empty the call is not timed
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    const bool timed = ctx->timing.enabled && ctx->timing.pool.size() >= 3;
+    if (timed) {
+        for (auto &e : ev) { e = ctx->timing.pool.back(); ctx->timing.pool.pop_back(); }
+        LVS_CUDA(cudaEventRecord(ev[0], ctx->stream));
+    }
+    // the key switch without its split form (whose partial sums would need scratch)
     LVS_CUDA(launch_keyswitch_plan(ctx, jobs, count, ms, nullptr, ks_plan(ctx, count), ctx->stream));
+    if (timed) LVS_CUDA(cudaEventRecord(ev[1], ctx->stream));
     LVS_CUDA(launch_blind_rotate(ctx, jobs, count, ms, d_lut, 1, ctx->stream));
+    if (timed) {
+        LVS_CUDA(cudaEventRecord(ev[2], ctx->stream));
+        ctx->timing.pending.push_back({ev[0], ev[1], ev[2], count});
+    }
     ctx->pbs_done += count;
-    ctx->launches += 3;
+    ctx->launches += 3;   // kernels launched: job fill, key switch, blind rotation
     return LVS_OK;
 }

@@ -70,6 +70,13 @@ __device__ __forceinline__ uint32_t redc(uint64_t T, uint32_t p, uint32_t pinv_n
     return (uint32_t)((T + (uint64_t)m * p) >> 32);
 }
 
+// value barrier: the compiler may not re-associate through it
+__device__ __forceinline__ uint32_t opaque(uint32_t x)
+{
+    asm("" : "+r"(x));
+    return x;
+}
+
 __device__ __forceinline__ void group_bar(int id, int nthreads)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -131,7 +138,7 @@ __device__ __forceinline__ void fwd_pass(uint32_t (&v)[NPA][8], uint32_t base, c
 #pragma unroll
                 for (int k = 0; k < NP; ++k) {
                     const uint32_t x = (FRESH && si == 0) ? v[k][q0] : csub(v[k][q0], p2);
-                    const uint32_t t = mul_shoup(w.x, w.y, v[k][q1], p);
+                    const uint32_t t = opaque(mul_shoup(w.x, w.y, v[k][q1], p));
                     v[k][q0] = x + t;
                     v[k][q1] = x - t + p2;
                 }
@@ -163,7 +170,7 @@ __device__ __forceinline__ void inv_pass(uint32_t (&v)[NPA][8], uint32_t base, c
                 for (int k = 0; k < NP; ++k) {
                     const uint32_t x = v[k][q0], y = v[k][q1];
                     v[k][q0] = csub(x + y, p2);
-                    v[k][q1] = mul_shoup(w.x, w.y, x - y + p2, p);
+                    v[k][q1] = opaque(mul_shoup(w.x, w.y, x - y + p2, p));
                 }
             }
         }

@@ -188,6 +188,7 @@ lvs_status lvs_ctx_autotune(lvs_ctx *ctx)
 lvs_status lvs_ctx_ks_plan(lvs_ctx *ctx, size_t njobs, int32_t *jobs_per_cta, int32_t *split)
 {
     if (!ctx || !jobs_per_cta || !split) return set_error(LVS_ERR_ARG, "lvs_ctx_ks_plan: NULL argument");
+    std::lock_guard<std::mutex> lock(ctx->mu);
     const KsPlan pl = ks_plan(ctx, njobs);
     *jobs_per_cta = pl.tj;
     *split = pl.split;
@@ -197,6 +198,7 @@ lvs_status lvs_ctx_ks_plan(lvs_ctx *ctx, size_t njobs, int32_t *jobs_per_cta, in
 lvs_status lvs_ctx_ks_gemm_min(lvs_ctx *ctx, size_t *min_jobs)
 {
     if (!ctx || !min_jobs) return set_error(LVS_ERR_ARG, "lvs_ctx_ks_gemm_min: NULL argument");
+    std::lock_guard<std::mutex> lock(ctx->mu);
     *min_jobs = ctx->ks_gemm ? ctx->ks_gemm_min : 0;
     return LVS_OK;
 }
@@ -214,6 +216,7 @@ lvs_status lvs_ctx_set_ks_gemm_min(lvs_ctx *ctx, size_t min_jobs)
 lvs_status lvs_ctx_max_launch_jobs(lvs_ctx *ctx, size_t *max_jobs)
 {
     if (!ctx || !max_jobs) return set_error(LVS_ERR_ARG, "lvs_ctx_max_launch_jobs: NULL argument");
+    std::lock_guard<std::mutex> lock(ctx->mu);
     *max_jobs = ctx->max_launch_jobs;
     return LVS_OK;
 }
@@ -232,6 +235,7 @@ lvs_status lvs_ctx_set_max_launch_jobs(lvs_ctx *ctx, size_t max_jobs)
 lvs_status lvs_ctx_br_split(lvs_ctx *ctx, size_t *max_jobs)
 {
     if (!ctx || !max_jobs) return set_error(LVS_ERR_ARG, "lvs_ctx_br_split: NULL argument");
+    std::lock_guard<std::mutex> lock(ctx->mu);
     *max_jobs = ctx->br_clusters > 0 ? ctx->br_split_max : 0;
     return LVS_OK;
 }

@@ -12,6 +12,8 @@ The bootstrapping-key noise adds n (k+1) l N E[d^2] var(TUniform(b_glwe)).
 import numpy as np
 import pytest
 
+from oracle import noise as Nz
+from oracle import tfhe as T
 from paper_2508_14568_gb300 import lvs as L
 
 pytestmark = pytest.mark.gpu
@@ -19,17 +21,15 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def tuniform_var(b):
-    return (2.0 ** (2 * b + 1) + 1) / 6.0
-
-
 def predicted_pbs_variance(p, lwe_key, glwe_key):
-    beta = p.pbs_level * p.pbs_base_log
-    B = 2 ** p.pbs_base_log
-    rnd = (2.0 ** (63 - beta)) ** 2 / 3.0                   # uniform on [-2^(63-beta), 2^(63-beta))
-    weight = float(np.sum(lwe_key)) * (1.0 + float(np.sum(glwe_key)))
-    bsk = p.n * (p.k + 1) * p.pbs_level * p.N * (B * B / 12.0) * tuniform_var(p.glwe_noise_log2)
-    return weight * rnd + bsk
+    """The oracle's bootstrap-output variance model (oracle.noise.var_pbs,
+    pinned against the oracle's own bootstraps) for the keys' actual
+    weights; p is the library's parameter set, which must be the oracle's."""
+    orc = T.params_lvs() if p.n == T.params_lvs().n else T.params_test()
+    pd = orc.as_dict()
+    for f in ("n", "k", "N", "pbs_level", "pbs_base_log", "glwe_noise_log2"):
+        assert pd[f] == getattr(p, f), f
+    return Nz.var_pbs(pd, float(np.sum(lwe_key)), float(np.sum(glwe_key)))
 
 
 def test_pbs_output_noise_matches_model():

@@ -136,7 +136,7 @@ def test_pbs_bit_exact_small_many(small):
     want = T.pbs_many(S.K, cts, np.asarray(luts, np.uint32))
     assert np.array_equal(got, want)
     for i in range(count):
-        assert T.decrypt(S.K, got[i]) == P.lookup(luts[i], int(msgs[i]))
+        assert T.decrypt(S.K, got[i]) == P.lookup([int(v) for v in luts[i]], int(msgs[i]))
 
 
 def test_pbs_bit_exact_full_params(full):
@@ -149,6 +149,33 @@ def test_pbs_bit_exact_full_params(full):
     assert np.array_equal(got, want)
     for i, m in enumerate(msgs):
         assert T.decrypt(S.K, got[i]) == P.lookup(luts[i], m)
+
+
+def test_pbs_one_cta_form_two_waves_full_params(full):
+    """The blind-rotation form the throughput launches use (one CTA per
+    ciphertext; the three-CTA form switched off) at the full parameters, on a
+    launch of 160 PBS: more than one wave of the persistent grid (one CTA per
+    SM), so jobs 152..159 are the second job of their CTA.  A sample of both
+    waves, with every kind of lookup table, is compared element by element
+    with the oracle's PBS of the same inputs."""
+    S = full
+    count = 160
+    rng = np.random.default_rng(77)
+    msgs = rng.integers(0, 32, size=count)
+    kinds = [P.LUT_MIN, P.LUT_EQ9, P.LUT_EQ, P.LUT_V, [(x - 4) % 32 for x in range(16)]]
+    luts = np.asarray([kinds[i % len(kinds)] for i in range(count)], np.uint32)
+    cts = np.stack([T.encrypt(S.K, int(m), 9, 0, i) for i, m in enumerate(msgs)])
+    split0 = L.lvs_ctx_br_split(S.ctx)
+    L.lvs_ctx_set_br_split(S.ctx, 0)
+    try:
+        got = _pbs_gpu(S, cts, luts)
+    finally:
+        L.lvs_ctx_set_br_split(S.ctx, split0)
+    sample = [0, 1, 75, 76, 150, 151] + list(range(152, 160))
+    want = T.pbs_many(S.K, cts[sample], luts[sample])
+    assert np.array_equal(got[sample], want)
+    for i in range(count):
+        assert T.decrypt(S.K, got[i]) == P.lookup(luts[i], int(msgs[i]))
 
 
 # ----------------------------------------------------------------- edit distance

@@ -147,14 +147,27 @@ def test_tensor_core_keyswitch_bit_exact(which):
     big = K.big_dim
     L.lvs_ctx_set_ks_gemm_min(ctx, 1)
     assert L.lvs_ctx_ks_gemm_min(ctx) == 1
-    for count in (1, 17, 300):
-        cts = np.stack([T.encrypt(K, (7 * i) % 32, 15, 4, i) for i in range(count)])
-        want = np.stack([T.modswitch(K, T.keyswitch(K, c)) for c in cts])
-        d_in = torch.from_numpy(cts.view(np.int64)).cuda()
+
+    def ks(d_in, count, gemm_min):
+        L.lvs_ctx_set_ks_gemm_min(ctx, gemm_min)
         d_out = torch.zeros((count, p.n + 1), dtype=torch.int32, device="cuda")
         L.lvs_keyswitch_batch_device(ctx, d_in, big + 1, d_out, count)
         L.lvs_ctx_synchronize(ctx)
-        assert np.array_equal(d_out.cpu().numpy().view(np.uint32), want), count
+        return d_out.cpu().numpy().view(np.uint32)
+
+    # 1, 17, 300 (ragged tiles): every output against the oracle;
+    # 4096 and 8300 (the second crosses the 8192-job pass of the digit
+    # scratch): every output against the kernel path (bit-exact with the oracle
+    # for every plan), and a sample against the oracle
+    for count in (1, 17, 300, 4096, 8300):
+        cts = np.stack([T.encrypt(K, (7 * i) % 32, 15, 4, i) for i in range(count)])
+        d_in = torch.from_numpy(cts.view(np.int64)).cuda()
+        got = ks(d_in, count, 1)
+        sample = range(count) if count <= 300 else sorted(set(range(0, count, count // 61)) | {count - 1})
+        want = np.stack([T.modswitch(K, T.keyswitch(K, cts[i])) for i in sample])
+        assert np.array_equal(got[list(sample)], want), count
+        if count > 300:
+            assert np.array_equal(got, ks(d_in, count, 0)), count
     if which == "test":
         pairs = [("kitten", "sitting"), ("abc", "abd"), ("flaw", "lawn")]
         A = [L.lvs_encrypt_string(ck, a, L.LVS_ALPHA_ASCII7, 16, 2 * k) for k, (a, b) in enumerate(pairs)]
