@@ -41,85 +41,78 @@ __device__ __forceinline__ uint64_t test_poly_at(const uint8_t (&f)[16], uint32_
     return neg ? 0 - v : v;
 }
 
-// Read-only load of key data that bypasses L1 (each key word is used once per
-// CMux; L1 keeps the twiddles instead).
-__device__ __forceinline__ uint4 ld_key(const uint4 *p)
-{
-    uint4 r;
-    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
-        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-        : "l"(p));
-    return r;
-}
-
-// External product core for prime group g: digit residues d (pass-0 layout,
-// in [0, 2p)) -> forward NTT -> Montgomery products with the key slice `key`
-// ([8][T][8] u32 for this prime, this thread at +tau*8) -> inverse NTT ->
+// External product core for prime group g: digit residues d (L0 layout, in
+// [0, p)) -> forward NTT -> Montgomery products with the key slice `key`
+// ([16][T][8] u32 for this prime, this thread at +tau*8) -> inverse NTT ->
 // residues of the two output polynomials written to out[j*N + e].
-template <int L>
-__device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][8], const uint32_t *__restrict__ key,
+// OUT_IN_BUF: out lies in this group's exchange buffer, so the group first
+// waits until every thread has read its last inverse exchange.
+template <int LOGN, bool OUT_IN_BUF = false>
+__device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][16], const uint32_t *__restrict__ key,
                                                  uint32_t *buf, uint32_t *out, uint32_t tau, int g,
-                                                 const uint2 *__restrict__ twf, const uint2 *__restrict__ twi,
-                                                 int bar_id)
+                                                 const uint2 *__restrict__ twf, const uint2 *__restrict__ twi)
 {
-    using G = Geo<L>;
-    constexpr int N = G::N, T = G::T;
-    const uint32_t p = c_pc.p[g], pinv = c_pc.pinv_neg[g];
-    ntt_forward4<L>(d, reinterpret_cast<uint4 *>(buf), tau, twf, p, bar_id);
+    using Lay = Layout<LOGN>;
+    constexpr int N = Lay::N, T = Lay::T;
+    const uint32_t p = c_pc.p[g], pinv = c_pc.pinv_neg[g], z = c_pc.zero;
+    ntt_forward4<LOGN>(d, reinterpret_cast<uint4 *>(buf), tau, twf, p, 1 + g, z);
 
-    // pointwise in the last layout (e = tau << 3 | q): out_c = sum_r D_r * K[r][c]
-    // (Montgomery), written over D_0, D_1
+    // pointwise: out_c = sum_r D_r * K[r][c] (Montgomery), written over D_0, D_1
     const uint4 *kp = reinterpret_cast<const uint4 *>(key + (size_t)tau * 8);
-    uint4 ka = ld_key(kp), kb = ld_key(kp + 1);
+    uint4 ka = __ldg(kp), kb = __ldg(kp + 1);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 16; ++q) {
         uint4 na, nb;
-        if (q + 1 < 8) {
+        if (q + 1 < 16) {
             const uint4 *np = kp + (size_t)(q + 1) * T * 2;
-            na = ld_key(np);
-            nb = ld_key(np + 1);
+            na = __ldg(np);
+            nb = __ldg(np + 1);
         }
         // transform values in [0, 4p) -> [0, 2p); key residues < p: each sum of
         // four products is below 8 p^2 < 2^63, REDC returns it below 3p, and one
         // more conditional subtraction gives the [0, 2p) the inverse expects
-        const uint32_t d0 = csub(d[0][q], 2 * p);
-        const uint32_t d1 = csub(d[1][q], 2 * p);
-        const uint32_t d2 = csub(d[2][q], 2 * p);
-        const uint32_t d3 = csub(d[3][q], 2 * p);
+        const uint32_t d0 = csubz(d[0][q], 2 * p, z);
+        const uint32_t d1 = csubz(d[1][q], 2 * p, z);
+        const uint32_t d2 = csubz(d[2][q], 2 * p, z);
+        const uint32_t d3 = csubz(d[3][q], 2 * p, z);
         // slot = row * 2 + column
         const uint64_t t0 = (uint64_t)d0 * ka.x + (uint64_t)d1 * ka.z + (uint64_t)d2 * kb.x + (uint64_t)d3 * kb.z;
         const uint64_t t1 = (uint64_t)d0 * ka.y + (uint64_t)d1 * ka.w + (uint64_t)d2 * kb.y + (uint64_t)d3 * kb.w;
-        d[0][q] = csub(redc(t0, p, pinv), 2 * p);
-        d[1][q] = csub(redc(t1, p, pinv), 2 * p);
-        if (q + 1 < 8) { ka = na; kb = nb; }
+        d[0][q] = csubz(redc(t0, p, pinv), 2 * p, z);
+        d[1][q] = csubz(redc(t1, p, pinv), 2 * p, z);
+        if (q + 1 < 16) { ka = na; kb = nb; }
     }
-    ntt_inverse2<L>(d, reinterpret_cast<uint2 *>(buf), tau, twi, p, bar_id);
+    ntt_inverse2<LOGN>(d, reinterpret_cast<uint2 *>(buf), tau, twi, p, 1 + g, z);
+    if (OUT_IN_BUF) {
+        if (T > 32) group_bar(1 + g, T); else __syncwarp();
+    }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const uint32_t e = tau | ((uint32_t)q << (L - 3));
-        out[0 * N + e] = csub(d[0][q], p);
-        out[1 * N + e] = csub(d[1][q], p);
+    for (int q = 0; q < 16; ++q) {
+        const uint32_t e = tau | ((uint32_t)q << Lay::B0);
+        out[0 * N + e] = csubz(d[0][q], p, z);
+        out[1 * N + e] = csubz(d[1][q], p, z);
     }
 }
 
-// Digit residues (mod this group's prime) of X^a ACC - ACC at the 8 positions
-// of the thread in the pass-0 layout (e = q << (L-3) | tau), for the mask
-// (j = 0) and body (j = 1) polynomials of the negacyclically extended
-// accumulator acc ([2][2N]).  Only the rounded top 2*base_log bits of x are
-// used: with shift = 64 - 2*base_log >= 32, (x + 2^(shift-1)) >> shift =
-// (hi32(x) + 2^(shift-33)) >> (shift-32).  Balanced digits with carry, least
-// significant level first; d < 0 is stored as d + p (<= p).
-template <int L>
-__device__ __forceinline__ void decompose(uint32_t (&d)[4][8], const uint64_t *acc, uint32_t a, uint32_t tau,
+// Digit residues (mod this group's prime) of X^a ACC - ACC at the 16 positions
+// of the thread in the L0 layout, for the mask (j = 0) and body (j = 1)
+// polynomials of the negacyclically extended accumulator acc ([2][2N]).
+// Only the rounded top 2*base_log bits of x are used: with
+// shift = 64 - 2*base_log >= 32, (x + 2^(shift-1)) >> shift =
+// (hi32(x) + 2^(shift-33)) >> (shift-32).  Balanced digits with carry,
+// least significant level first; d < 0 is stored as d + p (< 2p is fine).
+template <int LOGN>
+__device__ __forceinline__ void decompose(uint32_t (&d)[4][16], const uint64_t *acc, uint32_t a, uint32_t tau,
                                           uint32_t base_log, uint32_t pmB)
 {
-    constexpr int N = 1 << L;
+    using Lay = Layout<LOGN>;
+    constexpr int N = Lay::N;
     const uint32_t B = 1u << base_log, hB = B >> 1;
     const uint32_t hshift = 64 - 2 * base_log - 32;   // shift - 32
     const uint32_t hround = 1u << (hshift - 1);       // 2^(shift - 33)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const uint32_t e = tau | ((uint32_t)q << (L - 3));
+    for (int q = 0; q < 16; ++q) {
+        const uint32_t e = tau | ((uint32_t)q << Lay::B0);
         const uint32_t src = (e - a) & (2 * N - 1);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -162,40 +155,37 @@ __device__ __forceinline__ void sample_extract_epilogue(const Job &J, const uint
 }
 
 // ---------------------------------------------------------------- blind rotation
-// One CTA per ciphertext: three prime groups of T = N/8 threads (768 threads
-// at N = 2048), each group running its prime's transforms; the CRT and the
-// accumulator update are spread over the whole CTA.
 template <int LOGN>
 struct BrSmem {
     static constexpr int N = 1 << LOGN;
     static constexpr size_t acc_bytes = 2 * 2 * N * sizeof(uint64_t);   // negacyclically extended
-    static constexpr size_t buf_bytes = 3 * 4 * N * sizeof(uint32_t);
+    static constexpr size_t buf_bytes = 3 * (size_t)ExWords<LOGN>::WORDS * 16;
     static constexpr size_t crt_bytes = 3 * 2 * N * sizeof(uint32_t);
     static constexpr size_t total = acc_bytes + buf_bytes + crt_bytes;
 };
 
 template <int LOGN>
-__global__ void __launch_bounds__(3 * (1 << LOGN) / 8, 1)
+__global__ void __launch_bounds__(3 * (1 << LOGN) / 16, 1)
 k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__restrict__ ms, uint32_t n, const uint32_t *__restrict__ bsk,
                const uint2 *__restrict__ tw, const uint8_t *__restrict__ luts, int lut_per_job,
                uint32_t base_log)
 {
-    using G = Geo<LOGN>;
-    constexpr int N = G::N, T = G::T, NT = 3 * T;
+    using Lay = Layout<LOGN>;
+    constexpr int N = Lay::N, T = Lay::T, NT = 3 * T;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint64_t *acc = reinterpret_cast<uint64_t *>(smem_raw);
     uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw + BrSmem<LOGN>::acc_bytes);
-    uint32_t *crt = bufs + 3 * 4 * N;
+    uint32_t *crt = bufs + 3 * 4 * ExWords<LOGN>::WORDS;
 
     const int tid = threadIdx.x;
     const int g = tid / T;
     const uint32_t tau = tid % T;
-    uint32_t *buf = bufs + g * 4 * N;
+    uint32_t *buf = bufs + g * 4 * ExWords<LOGN>::WORDS;
     const uint32_t p = c_pc.p[g];
     const uint2 *twf = tw + (size_t)(g * 2 + 0) * N;
     const uint2 *twi = tw + (size_t)(g * 2 + 1) * N;
     const uint32_t pmB = p - (1u << base_log);
-    const size_t key_row = (size_t)3 * 8 * T * 8;   // u32 per BSK index i
+    const size_t key_row = (size_t)3 * 16 * T * 8;   // u32 per BSK index i
 
     for (uint32_t job = blockIdx.x; job < njobs; job += gridDim.x) {
         const Job J = jobs[job];
@@ -218,10 +208,10 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
         for (uint32_t i = 0; i < n; ++i) {
             const uint32_t a = __ldg(msj + i);
             if (a == 0) continue;   // X^0 ACC - ACC = 0: the external product is exactly 0
-            uint32_t d[4][8];
+            uint32_t d[4][16];
             decompose<LOGN>(d, acc, a, tau, base_log, pmB);
-            ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 8 * T * 8, buf, crt + g * 2 * N, tau,
-                                   g, twf, twi, 1 + g);
+            ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 16 * T * 8, buf, crt + g * 2 * N, tau,
+                                   g, twf, twi);
             __syncthreads();
             for (int c = tid; c < 2 * N; c += NT) {
                 const int j = c >> LOGN, e = c & (N - 1);
@@ -394,17 +384,15 @@ __global__ void k_ksk_colsum(const uint64_t *__restrict__ ksk, uint32_t rows, ui
 
 // ---------------------------------------------------------------- key conversion
 // BSK (coefficient domain, [i][row][col][N] u64) -> NTT domain
-// out[i][g][q][tau][slot = row*2+col] = NTT_p(row,col)[tau << 3 | q] * R * N^{-1} mod p
-// (the last-layout position of register q of thread tau: the order in which
-// the blind rotation's threads hold the transformed digits)
+// out[i][g][q][tau][slot = row*2+col] = NTT_p(row,col)[pos(tau,q)] * R * N^{-1} mod p
 template <int LOGN>
-__global__ void __launch_bounds__(3 * (1 << LOGN) / 8)
+__global__ void __launch_bounds__(3 * (1 << LOGN) / 16)
 k_bsk_to_ntt(const uint64_t *__restrict__ coef, uint32_t count, uint32_t *__restrict__ out,
              const uint2 *__restrict__ tw, uint32_t m0, uint32_t ms0, uint32_t m1, uint32_t ms1, uint32_t m2,
              uint32_t ms2)
 {
-    using G = Geo<LOGN>;
-    constexpr int N = G::N, T = G::T;
+    using Lay = Layout<LOGN>;
+    constexpr int N = Lay::N, T = Lay::T;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw);
     const int tid = threadIdx.x, g = tid / T;
@@ -412,22 +400,23 @@ k_bsk_to_ntt(const uint64_t *__restrict__ coef, uint32_t count, uint32_t *__rest
     const uint32_t i = blockIdx.x, h = blockIdx.y;   // h: slots 4h..4h+3
     if (i >= count) return;
     const uint32_t p = c_pc.p[g];
-    uint32_t v[4][8];
+    uint32_t v[4][16];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const uint32_t slot = 4 * h + k;   // = row * 2 + col
         const uint64_t *src = coef + ((size_t)i * 8 + slot) * N;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const uint32_t e = tau | ((uint32_t)q << (LOGN - 3));
+        for (int q = 0; q < 16; ++q) {
+            const uint32_t e = tau | ((uint32_t)q << Lay::B0);
             v[k][q] = residue_of_signed((int64_t)src[e], p);
         }
     }
-    ntt_forward4<LOGN>(v, reinterpret_cast<uint4 *>(bufs + g * 4 * N), tau, tw + (size_t)(g * 2) * N, p, 1 + g);
+    ntt_forward4<LOGN>(v, reinterpret_cast<uint4 *>(bufs + g * 4 * ExWords<LOGN>::WORDS), tau, tw + (size_t)(g * 2) * N,
+                       p, 1 + g, c_pc.zero);
     const uint32_t m = g == 0 ? m0 : (g == 1 ? m1 : m2), msh = g == 0 ? ms0 : (g == 1 ? ms1 : ms2);
-    uint32_t *dst = out + (size_t)i * 3 * 8 * T * 8 + (size_t)g * 8 * T * 8 + (size_t)tau * 8 + 4 * h;
+    uint32_t *dst = out + (size_t)i * 3 * 16 * T * 8 + (size_t)g * 16 * T * 8 + (size_t)tau * 8 + 4 * h;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 16; ++q) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const uint32_t x = csub(csub(v[k][q], 2 * p), p);
@@ -443,7 +432,9 @@ k_bsk_to_ntt(const uint64_t *__restrict__ coef, uint32_t count, uint32_t *__rest
 // work.  Each CTA keeps its own copy of the accumulator; after the inverse
 // transforms the residues are exchanged through distributed shared memory:
 // CTA g reconstructs every third block of coefficients from the three CTAs'
-// residues and writes the new values into all three accumulator copies.  Two
+// residues and writes the new values into all three accumulator copies.  The
+// residues are written into the CTA's exchange buffer once its threads have read
+// their last inverse exchange (two CTAs per SM fit).  Two
 // cluster barriers per CMux (residues ready; accumulators updated).  All CTAs
 // of a cluster run the same jobs and the same CMux sequence, so every CTA
 // reaches every cluster barrier.
@@ -451,25 +442,24 @@ template <int LOGN>
 struct BrClSmem {
     static constexpr int N = 1 << LOGN;
     static constexpr size_t acc_bytes = 2 * 2 * N * sizeof(uint64_t);
-    static constexpr size_t buf_bytes = 4 * N * sizeof(uint32_t);
-    static constexpr size_t res_bytes = 2 * N * sizeof(uint32_t);
-    static constexpr size_t total = acc_bytes + buf_bytes + res_bytes;
+    static constexpr size_t buf_bytes = (size_t)ExWords<LOGN>::WORDS * 16;   // the residues reuse it
+    static constexpr size_t total = acc_bytes + buf_bytes;
 };
 
 template <int LOGN>
-__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__((1 << LOGN) / 8, 2)
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__((1 << LOGN) / 16, 2)
 k_blind_rotate_cl(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__restrict__ ms, uint32_t n,
                   const uint32_t *__restrict__ bsk, const uint2 *__restrict__ tw, const uint8_t *__restrict__ luts,
                   int lut_per_job, uint32_t base_log)
 {
     namespace cg = cooperative_groups;
-    using G = Geo<LOGN>;
-    constexpr int N = G::N, T = G::T;
+    using Lay = Layout<LOGN>;
+    constexpr int N = Lay::N, T = Lay::T;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint64_t *acc = reinterpret_cast<uint64_t *>(smem_raw);
     uint32_t *buf = reinterpret_cast<uint32_t *>(smem_raw + BrClSmem<LOGN>::acc_bytes);
-    uint32_t *res = buf + 4 * N;                 // this prime's residues [2][N]
+    uint32_t *res = buf;   // this prime's residues [2][N], in the exchange buffer after the inverse
 
     const int g = (int)cl.block_rank();
     const uint32_t tau = threadIdx.x;
@@ -477,7 +467,7 @@ k_blind_rotate_cl(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *
     const uint2 *twf = tw + (size_t)(g * 2 + 0) * N;
     const uint2 *twi = tw + (size_t)(g * 2 + 1) * N;
     const uint32_t pmB = p - (1u << base_log);
-    const size_t key_row = (size_t)3 * 8 * T * 8;
+    const size_t key_row = (size_t)3 * 16 * T * 8;
     const uint32_t *res_of[3];
     uint64_t *acc_of[3];
 #pragma unroll
@@ -505,10 +495,10 @@ k_blind_rotate_cl(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *
         for (uint32_t i = 0; i < n; ++i) {
             const uint32_t a = __ldg(msj + i);
             if (a == 0) continue;   // the same for the three CTAs
-            uint32_t d[4][8];
+            uint32_t d[4][16];
             decompose<LOGN>(d, acc, a, tau, base_log, pmB);
-            ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 8 * T * 8, buf, res, tau, g, twf,
-                                   twi, 1);
+            ext_product_core<LOGN, true>(d, bsk + (size_t)i * key_row + (size_t)g * 16 * T * 8, buf, res, tau, g,
+                                         twf, twi);
             cl.sync();   // the three primes' residues are in place
             for (int c = g * T + (int)tau; c < 2 * N; c += 3 * T) {
                 const int j = c >> LOGN, e = c & (N - 1);
@@ -529,32 +519,32 @@ k_blind_rotate_cl(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *
 
 // Product-only kernel (parity of the NTT/CRT path): out[item] = sum_r dig[r] * key[r][col]
 template <int LOGN>
-__global__ void __launch_bounds__(3 * (1 << LOGN) / 8, 1)
+__global__ void __launch_bounds__(3 * (1 << LOGN) / 16, 1)
 k_poly_mul(const int32_t *__restrict__ dig, const uint32_t *__restrict__ keyntt, uint64_t *__restrict__ out,
            uint32_t count, const uint2 *__restrict__ tw)
 {
-    using G = Geo<LOGN>;
-    constexpr int N = G::N, T = G::T, NT = 3 * T;
+    using Lay = Layout<LOGN>;
+    constexpr int N = Lay::N, T = Lay::T, NT = 3 * T;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw + BrSmem<LOGN>::acc_bytes);
-    uint32_t *crt = bufs + 3 * 4 * N;
+    uint32_t *crt = bufs + 3 * 4 * ExWords<LOGN>::WORDS;
     const int tid = threadIdx.x, g = tid / T;
     const uint32_t tau = tid % T;
     const uint32_t item = blockIdx.x;
     if (item >= count) return;
     const uint32_t p = c_pc.p[g];
-    uint32_t d[4][8];
+    uint32_t d[4][16];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const uint32_t e = tau | ((uint32_t)q << (LOGN - 3));
+        for (int q = 0; q < 16; ++q) {
+            const uint32_t e = tau | ((uint32_t)q << Lay::B0);
             const int32_t x = dig[((size_t)item * 4 + r) * N + e];
             d[r][q] = x < 0 ? (uint32_t)(x + (int32_t)p) : (uint32_t)x;
         }
-    ext_product_core<LOGN>(d, keyntt + (size_t)item * 3 * 8 * T * 8 + (size_t)g * 8 * T * 8,
-                           bufs + g * 4 * N, crt + g * 2 * N, tau, g, tw + (size_t)(g * 2) * N,
-                           tw + (size_t)(g * 2 + 1) * N, 1 + g);
+    ext_product_core<LOGN>(d, keyntt + (size_t)item * 3 * 16 * T * 8 + (size_t)g * 16 * T * 8,
+                           bufs + g * 4 * ExWords<LOGN>::WORDS, crt + g * 2 * N, tau, g, tw + (size_t)(g * 2) * N,
+                           tw + (size_t)(g * 2 + 1) * N);
     __syncthreads();
     for (int c = tid; c < 2 * N; c += NT) {
         const int j = c >> LOGN, e = c & (N - 1);
@@ -578,9 +568,9 @@ __global__ void k_fill_trivial(uint64_t *arena, size_t stride, uint32_t big, siz
 // ---------------------------------------------------------------- host wrappers
 using namespace dev;
 
-int br_threads(uint32_t N) { return 3 * (int)N / 8; }
+int br_threads(uint32_t N) { return 3 * (int)N / 16; }
 int br_smem_bytes(uint32_t N) { return N == 2048 ? (int)BrSmem<11>::total : (int)BrSmem<9>::total; }
-size_t bsk_ntt_words(uint32_t n, uint32_t N) { return (size_t)n * 3 * 8 * (N / 8) * 8; }
+size_t bsk_ntt_words(uint32_t n, uint32_t N) { return (size_t)n * 3 * 16 * (N / 16) * 8; }
 
 cudaError_t upload_prime_consts(const PrimeConsts &pc) { return cudaMemcpyToSymbol(c_pc, &pc, sizeof(pc)); }
 
@@ -597,7 +587,7 @@ static cudaError_t set_attrs()
                              (int)BrClSmem<LOGN>::total);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_bsk_to_ntt<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(3 * 4 * (1 << LOGN) * sizeof(uint32_t)));
+                                (int)(3 * (size_t)ExWords<LOGN>::WORDS * 16));
 }
 
 template <int LOGN>
@@ -605,7 +595,7 @@ static int max_clusters()
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(3, 1, 1);
-    cfg.blockDim = dim3((1 << LOGN) / 8, 1, 1);
+    cfg.blockDim = dim3((1 << LOGN) / 16, 1, 1);
     cfg.dynamicSmemBytes = BrClSmem<LOGN>::total;
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeClusterDimension;
@@ -642,7 +632,7 @@ cudaError_t launch_bsk_to_ntt_count(uint32_t N, const uint64_t *coef, uint32_t c
     if (count == 0) return cudaSuccess;
     dim3 grid(count, 2);
     const uint2 *t2 = reinterpret_cast<const uint2 *>(tw);
-    const size_t sm = 3 * 4 * N * sizeof(uint32_t);
+    const size_t sm = 3 * (size_t)(N + N / 16) * 16;
     if (N == 2048)
         k_bsk_to_ntt<11><<<grid, br_threads(N), sm, s>>>(coef, count, out, t2, mont[0][0], mont[0][1], mont[1][0],
                                                           mont[1][1], mont[2][0], mont[2][1]);
@@ -719,10 +709,10 @@ cudaError_t launch_blind_rotate(const lvs_ctx *ctx, const Job *jobs, size_t njob
         // small launch: one ciphertext per cluster of three CTAs (one per prime)
         const unsigned grid = 3 * (unsigned)std::min<size_t>(njobs, (size_t)ctx->br_clusters);
         if (p.N == 2048)
-            k_blind_rotate_cl<11><<<grid, (1 << 11) / 8, BrClSmem<11>::total, s>>>(
+            k_blind_rotate_cl<11><<<grid, (1 << 11) / 16, BrClSmem<11>::total, s>>>(
                 jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log);
         else
-            k_blind_rotate_cl<9><<<grid, (1 << 9) / 8, BrClSmem<9>::total, s>>>(
+            k_blind_rotate_cl<9><<<grid, (1 << 9) / 16, BrClSmem<9>::total, s>>>(
                 jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log);
         return cudaGetLastError();
     }

@@ -12,22 +12,19 @@
 // Montgomery reduction (R = 2^32) for the key product, whose key operand is
 // stored pre-multiplied by R * N^{-1} so the inverse transform needs no scaling.
 //
-// Register layout: a prime group of T = N/8 threads holds 8 coefficients per
-// thread of up to four polynomials.  An N = 2^L point transform runs as
-// ceil(L/3) register passes of <= 3 radix-2 stages.  In pass k the register
-// index q (3 bits) sits at position bits [R, R + 3), R = max(L - 3 - 3k, 0),
-// and the thread index tau fills the other bits in order:
-//   e = (tau >> R) << (R + 3) | q << R | (tau & (2^R - 1)).
-// Pass 0 (R = L - 3) is e = q << (L - 3) | tau (coefficient order of the
-// accumulator); the last pass (R = 0) is e = tau << 3 | q.  The warp index
-// (tau >> 5) lands on position bits >= 8 in every pass but the first, so only
-// the exchange between pass 0 and pass 1 crosses warps (group barrier); the
-// others stay inside a warp.  The four forward polynomials of a position
-// travel as one 16-byte shared-memory word at swz16(e) = e ^ ((e >> 3) & 7),
-// the two inverse polynomials as one 8-byte word at idx8(e) (same per-warp
-// byte region as the 16-byte view); both are bank-conflict free in every
-// layout (each quarter-warp, resp. half-warp, of one store instruction lands
-// on distinct banks).
+// Register layout: a prime group of T = N/16 threads holds 16 coefficients per
+// thread of several polynomials.  An N-point transform runs as three register
+// passes of <= 4 radix-2 stages:
+//   L0: e = tau | q << (logN-4)           stages 0..3
+//   L1: e = hi << (logN-4) | q << (logN-8) | lo,   tau = hi << (logN-8) | lo
+//                                          stages 4..7
+//   L2: e = tau << 4 | q                   stages 8..logN-1
+// with shared-memory exchanges between passes.  The four forward polynomials
+// of a position travel as one 16-byte word (two inverse polynomials as one
+// 8-byte word), stored at the swizzled index e ^ ((e >> 4) & 7) (16 B) or
+// e ^ ((e >> 4) & 15) (8 B), which is bank-conflict free for all three
+// layouts.  L1 <-> L2 exchanges stay inside a warp; L0 <-> L1 needs the group
+// barrier.
 #pragma once
 #include <cstdint>
 
@@ -47,6 +44,7 @@ struct PrimeConsts {
     uint64_t p01;              // p0 p1 mod 2^64
     uint64_t m64;              // p0 p1 p2 mod 2^64
     uint32_t half2;            // p2 >> 1
+    uint32_t zero;             // 0, read at run time (see fwd_pass)
 };
 
 __device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m)
@@ -54,6 +52,11 @@ __device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t m)
     // x in [0, 2m) -> [0, m)
     return min(x, x - m);
 }
+
+// csub with a zero the compiler cannot see: x - m + z is a three-input add,
+// and the whole reduction becomes one fused add-and-minimum on the integer ALU
+// (with x - m alone the compiler may form the difference on the multiply pipe)
+__device__ __forceinline__ uint32_t csubz(uint32_t x, uint32_t m, uint32_t z) { return min(x, x - m + z); }
 
 // w * x mod p in [0, 2p) for any x < 2^32 (Shoup)
 __device__ __forceinline__ uint32_t mul_shoup(uint32_t w, uint32_t wsh, uint32_t x, uint32_t p)
@@ -70,7 +73,7 @@ __device__ __forceinline__ uint32_t redc(uint64_t T, uint32_t p, uint32_t pinv_n
     return (uint32_t)((T + (uint64_t)m * p) >> 32);
 }
 
-// value barrier: the compiler may not re-associate through it
+// value barrier: the compiler may not see through it
 __device__ __forceinline__ uint32_t opaque(uint32_t x)
 {
     asm("" : "+r"(x));
@@ -82,204 +85,196 @@ __device__ __forceinline__ void group_bar(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// Geometry of the register passes of an N = 2^L transform.
-template <int L>
-struct Geo {
-    static constexpr int N = 1 << L;
-    static constexpr int T = N / 8;                  // threads per prime group
-    static constexpr int PASSES = (L + 2) / 3;
-    static constexpr int R(int k) { return L - 3 - 3 * k > 0 ? L - 3 - 3 * k : 0; }
-    static constexpr int CNT(int k) { return L - 3 * k < 3 ? L - 3 * k : 3; }
+template <int LOGN>
+struct Layout {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int T = N / 16;
+    static constexpr int B0 = LOGN - 4;   // L0 register stride exponent
+    static constexpr int B1 = LOGN - 8;   // L1 register stride exponent
+    static constexpr int S2 = LOGN - 8;   // stages in the last pass
+    __device__ static __forceinline__ uint32_t base0(uint32_t tau) { return tau; }
+    __device__ static __forceinline__ uint32_t base1(uint32_t tau)
+    {
+        return ((tau >> B1) << (B1 + 4)) | (tau & ((1u << B1) - 1u));
+    }
+    __device__ static __forceinline__ uint32_t base2(uint32_t tau) { return tau << 4; }
 };
 
-// thread part of the position in the layout whose register field starts at bit R
-template <int L, int R>
-__device__ __forceinline__ uint32_t pass_base(uint32_t tau)
+// Position of register q (= qg << B) of the thread with base `base`, as far as
+// the twiddle index of stages s <= 3 needs it: in the L0 layout (B = LOGN - 4)
+// the thread bits lie below bit LOGN - 4 and are shifted out by
+// e >> (LOGN - s), so the index is the same for every thread (a compile-time
+// constant, one broadcast load).
+template <int LOGN, int B>
+__device__ __forceinline__ uint32_t tw_pos(uint32_t base, int qg)
 {
-    if (R == L - 3) return tau;   // pass 0: tau < 2^(L-3)
-    return ((tau >> R) << (R + 3)) | (tau & ((1u << R) - 1u));
+    return (B == LOGN - 4) ? ((uint32_t)qg << B) : (base | ((uint32_t)qg << B));
 }
 
-// 16-byte words: e ^ ((e >> 3) & 7).  8-byte words: the same per-warp byte
-// region as the 16-byte view (in the warp-local layouts warp w owns positions
-// e >> 8 == w, i.e. 16-byte words [256 w, 256 w + 256)), swizzled by
-// e ^ ((e >> 3) & 15) inside it.  Both maps are linear over GF(2), and base
-// and q << R occupy disjoint bits, so swz(base | q << R) = swz(base) ^
-// swz(q << R): the callers pass the thread part once and the register part is
-// a compile-time constant.
-__host__ __device__ __forceinline__ constexpr uint32_t swz16(uint32_t e) { return e ^ ((e >> 3) & 7u); }
-__host__ __device__ __forceinline__ constexpr uint32_t idx8(uint32_t e)
-{
-    return ((e >> 8) << 9) | ((e ^ ((e >> 3) & 15u)) & 255u);
-}
-
-// One register pass of forward (Cooley-Tukey) stages S0 .. S0+CNT-1 on NP
+// One register pass of forward (Cooley-Tukey) stages s0 .. s0+cnt-1 on NP
 // polynomials that share positions (and hence twiddles).  FRESH: the inputs of
-// the first stage are below 2p, so its lazy reduction is skipped (outputs stay
-// below 4p).  Stage s pairs positions e and e + 2^(L-1-s), twiddle index
-// 2^s + (e >> (L - s)).
-template <int L, int R, int S0, int CNT, int NP, int NPA, bool FRESH = false>
-__device__ __forceinline__ void fwd_pass(uint32_t (&v)[NPA][8], uint32_t base, const uint2 *__restrict__ tw,
-                                         uint32_t p)
+// the first stage are below 2p, so its lazy reduction can be skipped (outputs
+// stay below 4p).
+// z: a zero the compiler cannot see (from constant memory): adding it makes
+// every butterfly addition three-input, which keeps it on the integer ALU pipe
+// instead of letting the compiler fold it into the multiply-add pipe that the
+// Shoup products already saturate.
+template <int LOGN, int B, int S0, int CNT, int NP, int NPA, bool FRESH = false>
+__device__ __forceinline__ void fwd_pass(uint32_t (&v)[NPA][16], uint32_t base, const uint2 *__restrict__ tw,
+                                         uint32_t p, uint32_t z)
 {
-    const uint32_t p2 = 2 * p;
+    const uint32_t p2 = 2 * p, p2z = p2 + z;
 #pragma unroll
     for (int si = 0; si < CNT; ++si) {
         const int s = S0 + si;
-        const int rb = L - 1 - s - R;   // register bit of this stage's span
+        const int rb = LOGN - s - 1 - B;
 #pragma unroll
-        for (int g = 0; g < (1 << (2 - rb)); ++g) {
-            const uint32_t hi = (uint32_t)(g << (rb + 1)) << R;
-            const uint32_t pos = (R == L - 3) ? hi : (base | hi);   // pass 0: thread bits are shifted out
-            const uint2 w = __ldg(tw + (1u << s) + (pos >> (L - s)));
+        for (int g = 0; g < (1 << (3 - rb)); ++g) {
+            const uint2 w = __ldg(tw + (1u << s) + (tw_pos<LOGN, B>(base, g << (rb + 1)) >> (LOGN - s)));
 #pragma unroll
             for (int low = 0; low < (1 << rb); ++low) {
                 const int q0 = (g << (rb + 1)) | low, q1 = q0 | (1 << rb);
 #pragma unroll
                 for (int k = 0; k < NP; ++k) {
-                    const uint32_t x = (FRESH && si == 0) ? v[k][q0] : csub(v[k][q0], p2);
+                    const uint32_t x = (FRESH && si == 0) ? v[k][q0] : csubz(v[k][q0], p2, z);
                     const uint32_t t = opaque(mul_shoup(w.x, w.y, v[k][q1], p));
-                    v[k][q0] = x + t;
-                    v[k][q1] = x - t + p2;
+                    v[k][q0] = x + t + z;
+                    v[k][q1] = x + p2z - t;
                 }
             }
         }
     }
 }
 
-// One register pass of inverse (Gentleman-Sande) stages S0+CNT-1 .. S0 on the
-// first NP polynomials; values stay in [0, 2p).
-template <int L, int R, int S0, int CNT, int NP, int NPA>
-__device__ __forceinline__ void inv_pass(uint32_t (&v)[NPA][8], uint32_t base, const uint2 *__restrict__ tw,
-                                         uint32_t p)
+// One register pass of inverse (Gentleman-Sande) stages s0+cnt-1 .. s0.
+template <int LOGN, int B, int S0, int CNT, int NP, int NPA>
+__device__ __forceinline__ void inv_pass(uint32_t (&v)[NPA][16], uint32_t base, const uint2 *__restrict__ tw,
+                                         uint32_t p, uint32_t z)
 {
-    const uint32_t p2 = 2 * p;
+    const uint32_t p2 = 2 * p, p2z = p2 + z;
 #pragma unroll
     for (int si = CNT - 1; si >= 0; --si) {
         const int s = S0 + si;
-        const int rb = L - 1 - s - R;
+        const int rb = LOGN - s - 1 - B;
 #pragma unroll
-        for (int g = 0; g < (1 << (2 - rb)); ++g) {
-            const uint32_t hi = (uint32_t)(g << (rb + 1)) << R;
-            const uint32_t pos = (R == L - 3) ? hi : (base | hi);
-            const uint2 w = __ldg(tw + (1u << s) + (pos >> (L - s)));
+        for (int g = 0; g < (1 << (3 - rb)); ++g) {
+            const uint2 w = __ldg(tw + (1u << s) + (tw_pos<LOGN, B>(base, g << (rb + 1)) >> (LOGN - s)));
 #pragma unroll
             for (int low = 0; low < (1 << rb); ++low) {
                 const int q0 = (g << (rb + 1)) | low, q1 = q0 | (1 << rb);
 #pragma unroll
                 for (int k = 0; k < NP; ++k) {
                     const uint32_t x = v[k][q0], y = v[k][q1];
-                    v[k][q0] = csub(x + y, p2);
-                    v[k][q1] = opaque(mul_shoup(w.x, w.y, x - y + p2, p));
+                    const uint32_t s2 = x + y + z;
+                    v[k][q0] = csubz(s2, p2, z);
+                    v[k][q1] = opaque(mul_shoup(w.x, w.y, x + p2z - y, p));
                 }
             }
         }
     }
 }
 
-// shared-memory exchange of the thread's 8 positions (layout R, thread part sb
-// already swizzled): 4 polynomials per 16-byte word, 2 per 8-byte word
-template <int R, int NPA>
-__device__ __forceinline__ void st16(uint4 *buf, const uint32_t (&v)[NPA][8], uint32_t sb)
+// Shared-memory word of position e.  16-byte words (four forward polynomials):
+// w16(e) = e + (e >> 4), one padding word after every 16.  8-byte words (two
+// inverse polynomials): the same per-warp byte region as the 16-byte view (in
+// the L1 / L2 layouts warp w owns positions e >> 9 == w, i.e. 16-byte words
+// [544 w, 544 w + 544)): w8(e) = 1088 (e >> 9) + e' + (e' >> 4), e' = e & 511.
+// Both are bank-conflict free in the three layouts (the eight lanes of each
+// quarter-warp, resp. sixteen of each half-warp, of one access land on
+// distinct banks) and additive over disjoint bit fields: w(base | q << B) =
+// w(base) + w(q << B), so an access is the thread's base word plus a
+// compile-time offset that folds into the instruction's immediate.
+template <int LOGN>
+struct ExWords {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int WORDS = N + N / 16;   // 16-byte words per prime group
+};
+__device__ __forceinline__ constexpr uint32_t w16(uint32_t e) { return e + (e >> 4); }
+template <int LOGN>
+__device__ __forceinline__ constexpr uint32_t w8(uint32_t e)
 {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) buf[sb ^ swz16((uint32_t)q << R)] = make_uint4(v[0][q], v[1][q], v[2][q], v[3][q]);
+    return LOGN > 9 ? 1088u * (e >> 9) + (e & 511u) + ((e & 511u) >> 4) : e + (e >> 4);
 }
 
-template <int R, int NPA>
-__device__ __forceinline__ void ld16(const uint4 *buf, uint32_t (&v)[NPA][8], uint32_t sb)
+// store / load the polynomials of a thread in layout (B, base): 4 polynomials
+// per 16-byte word (forward) or 2 per 8-byte word (inverse); sb = the base's word
+template <int B, int NPA>
+__device__ __forceinline__ void st4(uint4 *buf, const uint32_t (&v)[NPA][16], uint32_t sb)
 {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const uint4 w = buf[sb ^ swz16((uint32_t)q << R)];
+    for (int q = 0; q < 16; ++q) buf[sb + w16((uint32_t)q << B)] = make_uint4(v[0][q], v[1][q], v[2][q], v[3][q]);
+}
+
+template <int B, int NPA>
+__device__ __forceinline__ void ld4(const uint4 *buf, uint32_t (&v)[NPA][16], uint32_t sb)
+{
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const uint4 w = buf[sb + w16((uint32_t)q << B)];
         v[0][q] = w.x; v[1][q] = w.y; v[2][q] = w.z; v[3][q] = w.w;
     }
 }
 
-template <int R, int NPA>
-__device__ __forceinline__ void st8(uint2 *buf, const uint32_t (&v)[NPA][8], uint32_t sb)
+template <int LOGN, int B, int NPA>
+__device__ __forceinline__ void st2(uint2 *buf, const uint32_t (&v)[NPA][16], uint32_t sb)
 {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) buf[sb ^ idx8((uint32_t)q << R)] = make_uint2(v[0][q], v[1][q]);
+    for (int q = 0; q < 16; ++q) buf[sb + w8<LOGN>((uint32_t)q << B)] = make_uint2(v[0][q], v[1][q]);
 }
 
-template <int R, int NPA>
-__device__ __forceinline__ void ld8(const uint2 *buf, uint32_t (&v)[NPA][8], uint32_t sb)
+template <int LOGN, int B, int NPA>
+__device__ __forceinline__ void ld2(const uint2 *buf, uint32_t (&v)[NPA][16], uint32_t sb)
 {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const uint2 w = buf[sb ^ idx8((uint32_t)q << R)];
+    for (int q = 0; q < 16; ++q) {
+        const uint2 w = buf[sb + w8<LOGN>((uint32_t)q << B)];
         v[0][q] = w.x; v[1][q] = w.y;
     }
 }
 
-// Passes 1 .. PASSES-1 of the forward transform (the caller has stored pass
-// 0's output and passed the group barrier).
-template <int L, int K>
-__device__ __forceinline__ void fwd_tail(uint32_t (&v)[4][8], uint4 *buf, uint32_t tau, const uint2 *__restrict__ tw,
-                                         uint32_t p)
+// Full forward transform of the 4 polynomials held in L0 layout (values in
+// [0, 2p)); returns them in L2 layout (bit-reversed evaluation order), values
+// in [0, 4p).
+// buf: ExWords<LOGN>::WORDS 16-byte words of this group's shared memory.  bar_id: group barrier.
+template <int LOGN>
+__device__ __forceinline__ void ntt_forward4(uint32_t (&v)[4][16], uint4 *buf, uint32_t tau,
+                                             const uint2 *__restrict__ tw, uint32_t p, int bar_id, uint32_t z)
 {
-    using G = Geo<L>;
-    constexpr int R = G::R(K);
-    const uint32_t b = pass_base<L, R>(tau);
-    const uint32_t sb = swz16(b);
-    ld16<R, 4>(buf, v, sb);
-    fwd_pass<L, R, 3 * K, G::CNT(K), 4, 4>(v, b, tw, p);
-    if constexpr (K + 1 < G::PASSES) {
-        __syncwarp();
-        st16<R, 4>(buf, v, sb);
-        __syncwarp();
-        fwd_tail<L, K + 1>(v, buf, tau, tw, p);
-    }
+    using Lay = Layout<LOGN>;
+    fwd_pass<LOGN, Lay::B0, 0, 4, 4, 4, true>(v, Lay::base0(tau), tw, p, z);
+    __syncwarp();
+    st4<Lay::B0, 4>(buf, v, w16(Lay::base0(tau)));
+    if (Lay::T > 32) group_bar(bar_id, Lay::T); else __syncwarp();
+    const uint32_t sb1 = w16(Lay::base1(tau));
+    ld4<Lay::B1, 4>(buf, v, sb1);
+    fwd_pass<LOGN, Lay::B1, 4, 4, 4, 4>(v, Lay::base1(tau), tw, p, z);
+    __syncwarp();
+    st4<Lay::B1, 4>(buf, v, sb1);
+    __syncwarp();
+    ld4<0, 4>(buf, v, w16(Lay::base2(tau)));
+    fwd_pass<LOGN, 0, 8, Lay::S2, 4, 4>(v, Lay::base2(tau), tw, p, z);
 }
 
-// Full forward transform of the 4 polynomials held in the pass-0 layout
-// (values in [0, 2p)); returns them in the last layout (bit-reversed
-// evaluation order, e = tau << 3 | q), values in [0, 4p).
-// buf: N 16-byte words of this group's shared memory.  bar_id / T: group barrier.
-template <int L>
-__device__ __forceinline__ void ntt_forward4(uint32_t (&v)[4][8], uint4 *buf, uint32_t tau,
-                                             const uint2 *__restrict__ tw, uint32_t p, int bar_id)
+// Inverse transform of the first 2 polynomials of v, held in L2 layout (values
+// in [0, 2p)); returns them in L0 layout (natural order), values in [0, 2p),
+// NOT scaled by N^{-1}.
+template <int LOGN>
+__device__ __forceinline__ void ntt_inverse2(uint32_t (&v)[4][16], uint2 *buf, uint32_t tau,
+                                             const uint2 *__restrict__ tw, uint32_t p, int bar_id, uint32_t z)
 {
-    using G = Geo<L>;
-    fwd_pass<L, L - 3, 0, 3, 4, 4, true>(v, tau, tw, p);
-    st16<L - 3, 4>(buf, v, swz16(tau));
-    if (G::T > 32) group_bar(bar_id, G::T); else __syncwarp();
-    fwd_tail<L, 1>(v, buf, tau, tw, p);
-}
-
-// Inverse passes K .. 0 of the first 2 polynomials, starting in layout K.
-template <int L, int K>
-__device__ __forceinline__ void inv_from(uint32_t (&v)[4][8], uint2 *buf, uint32_t tau, const uint2 *__restrict__ tw,
-                                         uint32_t p, int bar_id)
-{
-    using G = Geo<L>;
-    constexpr int R = G::R(K);
-    const uint32_t b = pass_base<L, R>(tau);
-    inv_pass<L, R, 3 * K, G::CNT(K), 2, 4>(v, b, tw, p);
-    if constexpr (K > 0) {
-        constexpr int R1 = G::R(K - 1);
-        const uint32_t b1 = pass_base<L, R1>(tau);
-        __syncwarp();
-        st8<R, 4>(buf, v, idx8(b));
-        if (K == 1) {
-            if (G::T > 32) group_bar(bar_id, G::T); else __syncwarp();
-        } else {
-            __syncwarp();
-        }
-        ld8<R1, 4>(buf, v, idx8(b1));
-        inv_from<L, K - 1>(v, buf, tau, tw, p, bar_id);
-    }
-}
-
-// Inverse transform of the first 2 polynomials of v, held in the last layout
-// (values in [0, 2p)); returns them in the pass-0 layout (natural order),
-// values in [0, 2p), NOT scaled by N^{-1}.
-template <int L>
-__device__ __forceinline__ void ntt_inverse2(uint32_t (&v)[4][8], uint2 *buf, uint32_t tau,
-                                             const uint2 *__restrict__ tw, uint32_t p, int bar_id)
-{
-    inv_from<L, Geo<L>::PASSES - 1>(v, buf, tau, tw, p, bar_id);
+    using Lay = Layout<LOGN>;
+    inv_pass<LOGN, 0, 8, Lay::S2, 2, 4>(v, Lay::base2(tau), tw, p, z);
+    __syncwarp();
+    st2<LOGN, 0, 4>(buf, v, w8<LOGN>(Lay::base2(tau)));
+    __syncwarp();
+    const uint32_t sb1 = w8<LOGN>(Lay::base1(tau));
+    ld2<LOGN, Lay::B1, 4>(buf, v, sb1);
+    inv_pass<LOGN, Lay::B1, 4, 4, 2, 4>(v, Lay::base1(tau), tw, p, z);
+    __syncwarp();
+    st2<LOGN, Lay::B1, 4>(buf, v, sb1);
+    if (Lay::T > 32) group_bar(bar_id, Lay::T); else __syncwarp();
+    ld2<LOGN, Lay::B0, 4>(buf, v, w8<LOGN>(Lay::base0(tau)));
+    inv_pass<LOGN, Lay::B0, 0, 4, 2, 4>(v, Lay::base0(tau), tw, p, z);
 }
 
 // Garner reconstruction of the signed integer with residues r0, r1, r2

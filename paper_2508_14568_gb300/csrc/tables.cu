@@ -98,6 +98,7 @@ void make_prime_consts(dev::PrimeConsts &pc)
     pc.p01 = (uint64_t)p0 * p1;
     pc.m64 = pc.p01 * p2;
     pc.half2 = p2 >> 1;
+    pc.zero = 0;
 }
 
 // R * N^{-1} mod p with R = 2^32, and its Shoup companion: the key is stored
