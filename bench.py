@@ -427,6 +427,7 @@ def run_lvs(args):
     sm_mhz_max = clk.get("sm_max_mhz") or 2070.0
     mul_lo, mul_hi = L.lvs_probe_int_mul(local)
     modmul_per_sm_clk = 1.0 / (2.0 / mul_lo + 1.0 / mul_hi)
+    shoup_stream, bfly_stream = L.lvs_probe_modmul(local)
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak = n_sms * modmul_per_sm_clk * sm_mhz_max * 1e6 / 1e12
     peak_mul32 = n_sms * MUL32_PER_SM_CLK * sm_mhz_max * 1e6 / 1e12
@@ -547,7 +548,15 @@ def run_lvs(args):
                                       "per SM per clk, lvs_probe_int_mul)" % (
                                           n_sms, modmul_per_sm_clk, sm_mhz_max, mul_lo, mul_hi),
                          "frac_all_mul_at_lo_rate": (3 * w_mod * units_per_launch / avg_launch_s / 1e12 / peak_mul32)
-                         if achieved else None},
+                         if achieved else None,
+                         "achievable": {
+                             "shoup_products_per_sm_clk": shoup_stream,
+                             "lazy_butterflies_per_sm_clk": bfly_stream,
+                             "frac_of_butterfly_stream": (achieved / (n_sms * bfly_stream * sm_mhz_max * 1e6 / 1e12))
+                             if achieved else None,
+                             "note": "lvs_probe_modmul: register-resident streams of Shoup products and of complete "
+                                     "lazy NTT butterflies (the kernel's form), one CTA per SM; what a kernel made "
+                                     "of these operations can reach, below the multiply issue rates of the peak"}},
             "kernels": {"blind_rotate": br, "keyswitch": ks,
                         "ks_plans": {"note": "launch size bucket end -> [PBS per CTA, split] (lvs_ctx_autotune)",
                                      "plans": ks_plans},

@@ -274,6 +274,21 @@ lvs_status lvs_plan_pair(size_t m, size_t n, uint32_t eq_lookups, int32_t band, 
  * symbol outside the alphabet or repeated gives LVS_ERR_ARG. */
 lvs_status lvs_plan_table(size_t m, lvs_alphabet alphabet, const uint8_t *subset, size_t nsub,
                           lvs_plan_layout *layout, lvs_plan_job *jobs, size_t *count);
+/* The launch schedule of a batch (host only, no GPU; the paper runs pairs one
+ * per thread, Section 6.2 "Parallelism": here the steps of many pairs share
+ * launches).  Pair p has the steps of lvs_plan_pair(m[p], n[p], eq_lookups,
+ * band); launch_of receives, pair after pair, the launch of each of its steps
+ * (count = total steps; launch_of NULL: size query), nlaunch the number of
+ * launches.  wave = 0: all pairs step together, launch s holding step s of
+ * every pair.  wave > 0: what batch calls do with wave = the blind-rotation
+ * grid (lvs_ctx_set_wave_fill): when a launch's PBS exceed a multiple of wave
+ * by r, pairs whose remaining steps are fewer than the longest pair's are
+ * held back one launch (smallest step first) until r PBS are held, so the
+ * launch ends on a full wave.  Either way a pair's steps are in increasing
+ * launches, and nlaunch is the longest pair's step count.  LVS_ERR_ARG for
+ * eq_lookups outside 1..2 or too little room. */
+lvs_status lvs_plan_batch(const size_t *m, const size_t *n, size_t npairs, uint32_t eq_lookups, int32_t band,
+                          size_t wave, int64_t *launch_of, size_t *count, size_t *nlaunch);
 
 /* Encrypted equality of characters a[i] and b[j] (Algorithm alg_ascii: 2 PBS
  * for ASCII7 / 27 symbols; Section 4.1: 1 PBS for DNA4).  times9 != 0 gives
@@ -491,6 +506,13 @@ lvs_status lvs_ctx_set_ks_plan(lvs_ctx *ctx, size_t njobs, int32_t jobs_per_cta,
  * off; LVS_ERR_STATE if the device cannot run it. */
 lvs_status lvs_ctx_br_split(lvs_ctx *ctx, size_t *max_jobs);
 lvs_status lvs_ctx_set_br_split(lvs_ctx *ctx, size_t max_jobs);
+/* Batch calls (lvs_edit_distance_batch, lvs_edit_distance_preprocessed_batch)
+ * hold short pairs back a launch when that ends the launch on a full wave of
+ * the blind-rotation grid (lvs_plan_batch with wave = the grid); on by
+ * default, 0 turns it off.  The schedule changes which launch runs a step,
+ * never a result: every pair's steps keep their order. */
+lvs_status lvs_ctx_set_wave_fill(lvs_ctx *ctx, int32_t enable);
+lvs_status lvs_ctx_wave_fill(lvs_ctx *ctx, int32_t *enabled);
 /* Key-switch launches of at least min_jobs PBS run as a dense product on the
  * tensor cores: digits (|d| <= 4) times the key-switching key split into its
  * eight bytes, one bf16 x bf16 -> fp32 product over the whole reduction
@@ -523,6 +545,15 @@ void lvs_debug_fail_allocations(int32_t count);
  * multiplication by a constant (Shoup) costs two low-half and one high-half
  * multiply.  Synchronous; allocates and frees its own buffers. */
 lvs_status lvs_probe_int_mul(int device, double *lo_per_sm_clk, double *hi_per_sm_clk);
+/* Achievable rates of the blind rotation's arithmetic on `device` (no
+ * counterpart in the paper; a measurement aid): modular multiplications by a
+ * constant (Shoup, the product of the NTT butterflies, Section 2.2's external
+ * product) and complete lazy NTT butterflies, each per SM per clock, from one
+ * CTA per SM of independent register-resident streams timed with the SM clock
+ * counter.  They bound what a kernel made of these operations can reach, below
+ * the multiply issue rates of lvs_probe_int_mul.  Synchronous; allocates and
+ * frees its own small buffers.  LVS_ERR_CUDA without a usable device. */
+lvs_status lvs_probe_modmul(int device, double *shoup_per_sm_clk, double *butterfly_per_sm_clk);
 
 /* Key switch + modulus switch only: d_out receives count * (n+1) uint32
  * values round(a * 2N / 2^64) of the key-switched ciphertexts. */

@@ -129,6 +129,39 @@ __device__ __forceinline__ void decompose(uint32_t (&d)[4][16], const uint64_t *
     }
 }
 
+// Digits of X^a ACC - ACC for all 2N coefficients, computed once for the CTA
+// instead of once per prime group (threads tid, tid + nthreads, ...), with the
+// rounding and balanced-digit rule of decompose(): the digit residues (d < 0
+// stored as d + p_g) of every prime g go into prime g's exchange buffer at the
+// 16-byte word of position e (pass-0 layout: level-1 and level-2 digits of the
+// mask, then of the body), from which each prime group loads its own positions.
+template <int LOGN>
+__device__ __forceinline__ void decompose_shared(uint32_t *bufs, const uint64_t *acc, uint32_t a, int tid,
+                                                 int nthreads, uint32_t base_log)
+{
+    constexpr int N = 1 << LOGN;
+    const uint32_t B = 1u << base_log, hB = B >> 1;
+    const uint32_t hshift = 64 - 2 * base_log - 32;
+    const uint32_t hround = 1u << (hshift - 1);
+    const uint32_t pm0 = c_pc.p[0] - B, pm1 = c_pc.p[1] - B, pm2 = c_pc.p[2] - B;
+    for (int c = tid; c < 2 * N; c += nthreads) {
+        const int j = c >> LOGN;
+        const uint32_t e = c & (N - 1);
+        const uint32_t src = (e - a) & (2 * N - 1);
+        const uint64_t *A = acc + j * 2 * N;
+        const uint64_t x = A[src] - A[e];
+        const uint32_t v = ((uint32_t)(x >> 32) + hround) >> hshift;
+        const uint32_t u2 = v & (B - 1);
+        const uint32_t c2 = u2 >> (base_log - 1);
+        const uint32_t r1 = (v >> base_log) + c2;
+        const uint32_t c1 = (r1 + hB) >> base_log;
+        const uint32_t w = w16(e) * 4 + 2 * j;   // u32 index of this component's two digits
+        *reinterpret_cast<uint2 *>(bufs + 0 * 4 * ExWords<LOGN>::WORDS + w) = make_uint2(r1 + c1 * pm0, u2 + c2 * pm0);
+        *reinterpret_cast<uint2 *>(bufs + 1 * 4 * ExWords<LOGN>::WORDS + w) = make_uint2(r1 + c1 * pm1, u2 + c2 * pm1);
+        *reinterpret_cast<uint2 *>(bufs + 2 * 4 * ExWords<LOGN>::WORDS + w) = make_uint2(r1 + c1 * pm2, u2 + c2 * pm2);
+    }
+}
+
 // Sample extract (coefficient 0) of the extended accumulator and the job's
 // epilogue: a_0 = A[0], a_u = -A[N - u] = A[2N - u] (u > 0), b = B[0]; a cell
 // job updates v[i] = M - h[i-1][j], h[j] = M - v[i][j-1] in place (and copies
@@ -181,10 +214,8 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
     const int g = tid / T;
     const uint32_t tau = tid % T;
     uint32_t *buf = bufs + g * 4 * ExWords<LOGN>::WORDS;
-    const uint32_t p = c_pc.p[g];
     const uint2 *twf = tw + (size_t)(g * 2 + 0) * N;
     const uint2 *twi = tw + (size_t)(g * 2 + 1) * N;
-    const uint32_t pmB = p - (1u << base_log);
     const size_t key_row = (size_t)3 * 16 * T * 8;   // u32 per BSK index i
 
     for (uint32_t job = blockIdx.x; job < njobs; job += gridDim.x) {
@@ -208,8 +239,12 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
         for (uint32_t i = 0; i < n; ++i) {
             const uint32_t a = __ldg(msj + i);
             if (a == 0) continue;   // X^0 ACC - ACC = 0: the external product is exactly 0
+            // digits once for the CTA into the exchange buffers; each prime group
+            // then loads its positions (the same words its first exchange rewrites)
+            decompose_shared<LOGN>(bufs, acc, a, tid, NT, base_log);
+            __syncthreads();
             uint32_t d[4][16];
-            decompose<LOGN>(d, acc, a, tau, base_log, pmB);
+            ld4<Lay::B0, 4>(reinterpret_cast<const uint4 *>(buf), d, w16(Lay::base0(tau)));
             ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 16 * T * 8, buf, crt + g * 2 * N, tau,
                                    g, twf, twi);
             __syncthreads();

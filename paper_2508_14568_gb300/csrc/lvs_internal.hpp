@@ -161,6 +161,7 @@ struct lvs_ctx {
     lvs::KsGemm *ks_gemm = nullptr;  // key switch on the tensor cores (null: unavailable)
     size_t ks_gemm_min = 0;          // launches of at least this many PBS use it (0: never)
     size_t max_launch_jobs = (size_t)1 << 16;   // wider wavefront steps run as several launches
+    bool wave_fill = true;         // batch calls hold pairs back to end launches on full waves
     uint64_t pbs_done = 0;
     uint64_t launches = 0;
     lvs::Timing timing;
@@ -292,6 +293,11 @@ void table_step_jobs(int step, uint32_t C, size_t m, const std::vector<std::pair
             }
         }
 }
+// launch index of every step of every pair from the PBS count of each step: the
+// launches fill the waves of a grid of `wave` concurrent jobs (0: all pairs step
+// together); nlaunch = number of launches
+void schedule_steps(const std::vector<std::vector<uint32_t>> &counts, size_t wave,
+                    std::vector<std::vector<long>> &launch_of, long *nlaunch);
 // jobs of wavefront step s of one pair (cells of anti-diagonal s - depth, etc.)
 void plan_pair_step(const PairRows &P, const Arena &A, long s, std::vector<Job> &jobs);
 // number of steps of one pair (0 if it has no cell)

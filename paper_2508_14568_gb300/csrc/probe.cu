@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "lvs_internal.hpp"
+#include "ntt.cuh"
 
 namespace lvs {
 
@@ -47,9 +48,122 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_mul(uint32_t *out, long
     if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// Achievable rates of the blind rotation's arithmetic, in the form the NTT
+// runs it: a stream of Shoup products (MODE 0) and a stream of complete lazy
+// forward butterflies (MODE 1: reduction, product, two additions, with the run-time
+// zero of the kernel's butterflies).  Each thread holds 32 independent values and
+// 16 twiddle pairs in registers and runs radix-2 stages of 16 butterflies, so no
+// address arithmetic enters the loop.  768 threads, one CTA per SM.
+constexpr int kModThreads = 768;
+constexpr int kModIters = 256;
+
+template <int MODE>
+__global__ void __launch_bounds__(kModThreads) k_probe_modmul(uint32_t *out, long long *cycles, const uint2 *tw,
+                                                              uint32_t p, uint32_t z)
+{
+    uint32_t v[32], w[16], ws[16];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = (threadIdx.x * 32u + i) % (2 * p);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const uint2 t = tw[(threadIdx.x + i) & 1023];
+        w[i] = t.x;
+        ws[i] = t.y;
+    }
+    const uint32_t p2 = 2 * p, p2z = p2 + z;
+    __syncthreads();
+    const long long t0 = clock64();
+#pragma unroll 1
+    for (int it = 0; it < kModIters; ++it) {
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const int h = 16 >> s;
+#pragma unroll
+            for (int g = 0; g < (1 << s); ++g) {
+                const int ti = ((1 << s) + g) & 15;
+#pragma unroll
+                for (int j = 0; j < h; ++j) {
+                    uint32_t &a = v[g * 2 * h + j], &b = v[g * 2 * h + j + h];
+                    if (MODE == 0) {
+                        b = dev::opaque(dev::mul_shoup(w[ti], ws[ti], b, p));
+                        a = a + z;
+                    } else {
+                        const uint32_t x = dev::csubz(a, p2, z);
+                        const uint32_t t = dev::opaque(dev::mul_shoup(w[ti], ws[ti], b, p));
+                        a = x + t + z;
+                        b = x + p2z - t;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc += v[i];
+    out[(size_t)blockIdx.x * kModThreads + threadIdx.x] = acc;
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 }  // namespace lvs
 
 using namespace lvs;
+
+extern "C" lvs_status lvs_probe_modmul(int device, double *shoup_per_sm_clk, double *butterfly_per_sm_clk)
+{
+    if (!shoup_per_sm_clk || !butterfly_per_sm_clk) return set_error(LVS_ERR_ARG, "lvs_probe_modmul: NULL argument");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return set_error(LVS_ERR_CUDA, "lvs_probe_modmul: no such CUDA device");
+    }
+    LVS_CUDA(cudaSetDevice(device));
+    int sms = 0;
+    LVS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    const uint32_t p = kPrime[0];
+    std::vector<uint2> htw(1024);
+    for (uint32_t i = 0; i < 1024; ++i) {
+        const uint32_t w = (uint32_t)((1234567ull * (i + 1)) % p);
+        htw[i] = make_uint2(w, (uint32_t)(((uint64_t)w << 32) / p));
+    }
+    uint32_t *out = nullptr;
+    long long *cyc = nullptr;
+    uint2 *tw = nullptr;
+    if (cudaMalloc((void **)&out, (size_t)sms * kModThreads * 4) != cudaSuccess ||
+        cudaMalloc((void **)&cyc, (size_t)sms * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc((void **)&tw, htw.size() * sizeof(uint2)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(out);
+        cudaFree(cyc);
+        return set_error(LVS_ERR_OOM, "lvs_probe_modmul: device allocation failed");
+    }
+    cudaError_t e = cudaMemcpy(tw, htw.data(), htw.size() * sizeof(uint2), cudaMemcpyHostToDevice);
+    double rate[2] = {0, 0};
+    std::vector<long long> h(sms);
+    void (*kern[2])(uint32_t *, long long *, const uint2 *, uint32_t, uint32_t) = {k_probe_modmul<0>,
+                                                                                   k_probe_modmul<1>};
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        e = cudaFuncSetAttribute(kern[v], cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem);
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first run warms up
+            kern[v]<<<sms, kModThreads, kProbeSmem>>>(out, cyc, tw, p, 0u);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, sms * sizeof(long long), cudaMemcpyDeviceToHost);
+        }
+        if (e == cudaSuccess) {
+            std::sort(h.begin(), h.end());
+            const double ops = (double)kModThreads * kModIters * 5 * 16;   // products or butterflies
+            rate[v] = ops / (double)h[sms / 2];
+        }
+    }
+    cudaFree(out);
+    cudaFree(cyc);
+    cudaFree(tw);
+    if (e != cudaSuccess) return cuda_error(e, "lvs_probe_modmul");
+    *shoup_per_sm_clk = rate[0];
+    *butterfly_per_sm_clk = rate[1];
+    return LVS_OK;
+}
 
 extern "C" lvs_status lvs_probe_int_mul(int device, double *lo_per_sm_clk, double *hi_per_sm_clk)
 {

@@ -214,14 +214,87 @@ long pair_steps(const PairRows &P)
 }
 
 // Runs the wavefront over all pairs; rows already placed.
+// Launch of every step of every pair.  All pairs start together; at each
+// launch, when the PBS of the pairs' current steps exceed a multiple of `wave`
+// (the jobs the blind-rotation grid runs at once) by a remainder r, pairs with
+// slack -- whose remaining steps are fewer than the longest pair's -- are held
+// back one launch, smallest current step first, until at least r PBS are held
+// back: the launch then ends on a full wave and the held-back steps join later
+// launches.  A pair's steps keep their order (each launch runs at most one step
+// of a pair, after its earlier steps), and the number of launches stays the
+// longest pair's step count.  wave == 0: no holding back.
+void schedule_steps(const std::vector<std::vector<uint32_t>> &counts, size_t wave,
+                    std::vector<std::vector<long>> &launch_of, long *nlaunch)
+{
+    const size_t np = counts.size();
+    launch_of.assign(np, {});
+    std::vector<size_t> cur(np, 0);
+    for (size_t p = 0; p < np; ++p) launch_of[p].assign(counts[p].size(), -1);
+    std::vector<size_t> act, cand;
+    std::vector<char> held(np, 0);
+    long t = 0;
+    for (;; ++t) {
+        act.clear();
+        size_t rem_max = 0, tot = 0;
+        for (size_t p = 0; p < np; ++p)
+            if (cur[p] < counts[p].size()) {
+                act.push_back(p);
+                rem_max = std::max(rem_max, counts[p].size() - cur[p]);
+                tot += counts[p][cur[p]];
+            }
+        if (act.empty()) break;
+        const size_t r = wave ? tot % wave : 0;
+        if (wave && tot > wave && r > 0) {
+            cand.clear();
+            for (size_t p : act)
+                if (counts[p].size() - cur[p] < rem_max && counts[p][cur[p]] > 0) cand.push_back(p);
+            std::stable_sort(cand.begin(), cand.end(),
+                             [&](size_t x, size_t y) { return counts[x][cur[x]] < counts[y][cur[y]]; });
+            size_t s = 0;
+            for (size_t p : cand) {
+                if (s >= r) break;
+                held[p] = 1;
+                s += counts[p][cur[p]];
+            }
+        }
+        for (size_t p : act) {
+            if (held[p]) { held[p] = 0; continue; }
+            launch_of[p][cur[p]] = t;
+            ++cur[p];
+        }
+    }
+    *nlaunch = t;
+}
+
 static lvs_status run_wavefront(lvs_ctx *ctx, const std::vector<PairRows> &pairs, const Arena &A, bool use_graph)
 {
-    long steps = 0;
-    for (const auto &P : pairs) steps = std::max(steps, pair_steps(P));
+    const size_t np = pairs.size();
+    // every step of every pair, planned once
+    std::vector<std::vector<Job>> pj(np);
+    std::vector<std::vector<size_t>> poff(np);
+    std::vector<std::vector<uint32_t>> counts(np);
+    for (size_t p = 0; p < np; ++p) {
+        const long steps = pair_steps(pairs[p]);
+        poff[p].push_back(0);
+        for (long s = 0; s < steps; ++s) {
+            plan_pair_step(pairs[p], A, s, pj[p]);
+            poff[p].push_back(pj[p].size());
+            counts[p].push_back((uint32_t)(poff[p][s + 1] - poff[p][s]));
+        }
+    }
+    std::vector<std::vector<long>> launch_of;
+    long nl = 0;
+    schedule_steps(counts, ctx->wave_fill ? (size_t)ctx->br_grid : 0, launch_of, &nl);
+    // launch t = the steps scheduled at t, in pair order
+    std::vector<std::vector<std::pair<size_t, size_t>>> at(nl);
+    for (size_t p = 0; p < np; ++p)
+        for (size_t s = 0; s < launch_of[p].size(); ++s) at[launch_of[p][s]].push_back({p, s});
     std::vector<Job> jobs;
     std::vector<size_t> off{0};
-    for (long s = 0; s < steps; ++s) {
-        for (const auto &P : pairs) plan_pair_step(P, A, s, jobs);
+    for (long t = 0; t < nl; ++t) {
+        for (const auto &ps : at[t])
+            jobs.insert(jobs.end(), pj[ps.first].begin() + poff[ps.first][ps.second],
+                        pj[ps.first].begin() + poff[ps.first][ps.second + 1]);
         off.push_back(jobs.size());
     }
     return run_steps(ctx, jobs, off, use_graph);
@@ -575,6 +648,39 @@ lvs_status lvs_plan_pair(size_t m, size_t n, uint32_t eq_lookups, int32_t band, 
     if (!jobs) return LVS_OK;
     if (room < J.size()) return set_error(LVS_ERR_ARG, "lvs_plan_pair: jobs has too little room");
     export_jobs(J, step_of, A.d, jobs);
+    return LVS_OK;
+}
+
+lvs_status lvs_plan_batch(const size_t *m, const size_t *n, size_t npairs, uint32_t eq_lookups, int32_t band,
+                          size_t wave, int64_t *launch_of, size_t *count, size_t *nlaunch)
+{
+    if (!count || !nlaunch || (npairs && (!m || !n))) return set_error(LVS_ERR_ARG, "lvs_plan_batch: NULL argument");
+    if (eq_lookups < 1 || eq_lookups > 2) return set_error(LVS_ERR_ARG, "lvs_plan_batch: eq_lookups must be 1 or 2");
+    std::vector<std::vector<uint32_t>> counts(npairs);
+    size_t total = 0;
+    for (size_t p = 0; p < npairs; ++p) {
+        size_t cnt = 0;
+        lvs_status st = lvs_plan_pair(m[p], n[p], eq_lookups, band, nullptr, nullptr, nullptr, 0, nullptr, nullptr, &cnt);
+        if (st != LVS_OK) return st;
+        std::vector<lvs_plan_job> J(std::max<size_t>(1, cnt));
+        lvs_plan_layout L;
+        st = lvs_plan_pair(m[p], n[p], eq_lookups, band, nullptr, nullptr, nullptr, 0, &L, J.data(), &cnt);
+        if (st != LVS_OK) return st;
+        counts[p].assign((size_t)L.steps, 0);
+        for (size_t k = 0; k < cnt; ++k) counts[p][(size_t)J[k].step] += 1;
+        total += (size_t)L.steps;
+    }
+    std::vector<std::vector<long>> lo;
+    long nl = 0;
+    schedule_steps(counts, wave, lo, &nl);
+    const size_t room = *count;
+    *count = total;
+    *nlaunch = (size_t)nl;
+    if (!launch_of) return LVS_OK;
+    if (room < total) return set_error(LVS_ERR_ARG, "lvs_plan_batch: launch_of has too little room");
+    size_t k = 0;
+    for (size_t p = 0; p < npairs; ++p)
+        for (long v : lo[p]) launch_of[k++] = v;
     return LVS_OK;
 }
 

@@ -232,6 +232,22 @@ lvs_status lvs_ctx_set_max_launch_jobs(lvs_ctx *ctx, size_t max_jobs)
     return LVS_OK;
 }
 
+lvs_status lvs_ctx_set_wave_fill(lvs_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return set_error(LVS_ERR_ARG, "lvs_ctx_set_wave_fill: NULL context");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->wave_fill = enable != 0;
+    return LVS_OK;
+}
+
+lvs_status lvs_ctx_wave_fill(lvs_ctx *ctx, int32_t *enabled)
+{
+    if (!ctx || !enabled) return set_error(LVS_ERR_ARG, "lvs_ctx_wave_fill: NULL argument");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    *enabled = ctx->wave_fill ? 1 : 0;
+    return LVS_OK;
+}
+
 lvs_status lvs_ctx_br_split(lvs_ctx *ctx, size_t *max_jobs)
 {
     if (!ctx || !max_jobs) return set_error(LVS_ERR_ARG, "lvs_ctx_br_split: NULL argument");

@@ -38,8 +38,10 @@ EXPORTS = [
     "lvs_poly_mul_device", "lvs_ctx_set_timing", "lvs_ctx_kernel_stats", "lvs_ctx_pbs_count",
     "lvs_ctx_launch_count", "lvs_ct_string_upload", "lvs_pbs_batch_device_noalloc",
     "lvs_ctx_prepare_fft64", "lvs_pbs_batch_device_fft64", "lvs_noise_budget", "lvs_noise_plan",
-    "lvs_ctx_autotune", "lvs_ctx_ks_plan", "lvs_ctx_set_ks_plan", "lvs_probe_int_mul", "lvs_preprocess_batch",
-    "lvs_ct_string_pin", "lvs_ctx_br_split", "lvs_ctx_set_br_split",
+    "lvs_ctx_autotune", "lvs_ctx_ks_plan", "lvs_ctx_set_ks_plan", "lvs_probe_int_mul", "lvs_probe_modmul",
+    "lvs_preprocess_batch",
+    "lvs_ct_string_pin", "lvs_ctx_br_split", "lvs_ctx_set_br_split", "lvs_ctx_set_wave_fill", "lvs_ctx_wave_fill",
+    "lvs_plan_batch",
     "lvs_noise_pfail", "lvs_debug_fail_allocations", "lvs_ctx_ks_gemm_min", "lvs_ctx_set_ks_gemm_min",
     "lvs_server_create", "lvs_server_submit", "lvs_server_poll", "lvs_server_stats_get", "lvs_server_free",
 ]
@@ -167,6 +169,10 @@ def _declare(L):
         "lvs_ctx_set_max_launch_jobs": ([vp, sz], i32),
         "lvs_ctx_set_br_split": ([vp, sz], i32),
         "lvs_preprocess_batch": ([vp, vpp, sz, ctypes.c_char_p, sz, vpp], i32),
+        "lvs_ctx_set_wave_fill": ([vp, i32], i32),
+        "lvs_ctx_wave_fill": ([vp, ctypes.POINTER(i32)], i32),
+        "lvs_plan_batch": ([szp, szp, sz, u32, i32, sz, ctypes.POINTER(ctypes.c_int64), szp, szp], i32),
+        "lvs_probe_modmul": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
         "lvs_probe_int_mul": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
         "lvs_ctx_ks_plan": ([vp, sz, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "lvs_ctx_set_ks_plan": ([vp, sz, i32, i32], i32),
@@ -334,6 +340,34 @@ def lvs_plan_pair(m, n, eq_lookups, band=-1, refresh=None, plain=None, subset=No
 def _plan_jobs(jobs, n):
     return [{"step": j.step, "src": list(j.src), "coef": list(j.coef), "cst": j.cst, "dst": list(j.dst),
              "tap": j.tap, "lut": j.lut, "kind": j.kind, "tapsel": j.tapsel} for j in jobs[:n]]
+
+
+def lvs_plan_batch(sizes, eq_lookups, band=-1, wave=0):
+    """sizes: [(m, n), ...].  Returns (launch of every step, per pair as a
+    list, number of launches) of the batch schedule (host only)."""
+    np_ = len(sizes)
+    m = (ctypes.c_size_t * max(1, np_))(*[a for a, b in sizes])
+    n = (ctypes.c_size_t * max(1, np_))(*[b for a, b in sizes])
+    cnt, nl = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    _check(lib().lvs_plan_batch(m, n, np_, eq_lookups, band, wave, None, ctypes.byref(cnt), ctypes.byref(nl)))
+    out = (ctypes.c_int64 * max(1, cnt.value))()
+    _check(lib().lvs_plan_batch(m, n, np_, eq_lookups, band, wave, out, ctypes.byref(cnt), ctypes.byref(nl)))
+    res, k = [], 0
+    for a, b in sizes:
+        steps = lvs_plan_pair(a, b, eq_lookups, band)[0]["steps"]
+        res.append(list(out[k:k + steps]))
+        k += steps
+    return res, nl.value
+
+
+def lvs_ctx_set_wave_fill(ctx, enable):
+    _check(lib().lvs_ctx_set_wave_fill(ctx, 1 if enable else 0))
+
+
+def lvs_ctx_wave_fill(ctx):
+    v = ctypes.c_int32()
+    _check(lib().lvs_ctx_wave_fill(ctx, ctypes.byref(v)))
+    return bool(v.value)
 
 
 def lvs_plan_table(m, alphabet, subset):
@@ -638,6 +672,13 @@ def lvs_probe_int_mul(device=0):
     lo, hi = ctypes.c_double(), ctypes.c_double()
     _check(lib().lvs_probe_int_mul(device, ctypes.byref(lo), ctypes.byref(hi)))
     return lo.value, hi.value
+
+
+def lvs_probe_modmul(device=0):
+    """(Shoup products, lazy NTT butterflies) per SM per clock, measured."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().lvs_probe_modmul(device, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def lvs_ctx_autotune(ctx):

@@ -245,6 +245,25 @@ def test_graph_and_direct_launches_identical(small):
         assert np.array_equal(L.lvs_result_export(r1, k, small.big), L.lvs_result_export(r2, k, small.big))
 
 
+def test_wave_fill_schedule_changes_no_ciphertext(small):
+    """Holding pairs back to fill the waves of the blind-rotation grid moves
+    steps between launches but never a result: every result row is bit-equal
+    to the all-pairs-together schedule's, on a batch wide enough that pairs
+    are held back, and the distances equal WF."""
+    S = small
+    pairs = W.random_pairs(29, 90, W.PRINTABLE, 4, 18)
+    L.lvs_ctx_set_wave_fill(S.ctx, True)
+    r1, d1 = _gpu_batch(S, pairs, P.ALPHA_ASCII7, seed=57)
+    L.lvs_ctx_set_wave_fill(S.ctx, False)
+    try:
+        r2, d2 = _gpu_batch(S, pairs, P.ALPHA_ASCII7, seed=57)
+    finally:
+        L.lvs_ctx_set_wave_fill(S.ctx, True)
+    assert d1 == d2 == [P.wf_distance(a, b) for a, b in pairs]
+    for k in range(len(pairs)):
+        assert np.array_equal(L.lvs_result_export(r1, k, S.big), L.lvs_result_export(r2, k, S.big))
+
+
 def test_full_params_one_cell_chain_bit_exact(full):
     """Full parameter set, one ASCII pair of single characters: EQ1 -> EQ9 ->
     cell, every ciphertext of the chain bit-exact (the readout row)."""

@@ -81,6 +81,18 @@ def test_int_mul_probe_plausible():
     assert hi <= lo * 1.05
 
 
+def test_modmul_probe_below_the_multiply_issue_rates():
+    """The achievable rates of the NTT's arithmetic: a Shoup product needs two
+    low-half and one high-half multiply, so its stream cannot beat the issue
+    rates of lvs_probe_int_mul (5% slack for timing), and a complete lazy
+    butterfly (a product plus three additions) is no faster than a product."""
+    lo, hi = L.lvs_probe_int_mul(0)
+    shoup, bfly = L.lvs_probe_modmul(0)
+    bound = 1.0 / (2.0 / lo + 1.0 / hi)
+    assert 1.0 <= bfly <= shoup * 1.05
+    assert shoup <= bound * 1.05
+
+
 @pytest.mark.parametrize("which", ["test", "default"])
 def test_three_cta_blind_rotation_bit_exact(which):
     """The blind rotation split over a cluster of three CTAs (one per NTT

@@ -231,3 +231,49 @@ def test_table_plan_argument_errors():
         L.lvs_plan_table(3, L.LVS_ALPHA_27, "Ab")        # lowercase outside the alphabet
     with pytest.raises(L.LvsError):
         L.lvs_plan_table(3, L.LVS_ALPHA_DNA4, "ACA")     # repeated
+
+
+# --------------------------------------------------------------- batch schedule
+
+@pytest.mark.parametrize("eq_lookups,band", [(2, -1), (1, -1), (2, 3)])
+def test_batch_schedule_keeps_each_pair_in_order_and_fills_waves(eq_lookups, band):
+    """The batch call's launch schedule (lvs_plan_batch): every pair's steps
+    run in increasing launches (one step of a pair per launch, so each step
+    sees all of its own earlier steps done), the launch count is the longest
+    pair's step count, every job is scheduled once, and holding pairs back
+    never needs more waves of the grid than stepping all pairs together."""
+    rng = random.Random(41 + eq_lookups + band)
+    wave = 152
+    for trial in range(4):
+        sizes = [(rng.randint(1, 20), rng.randint(1, 20)) for _ in range(rng.randint(30, 120))]
+        if band >= 0:
+            sizes = [(a, a) for a, b in sizes]          # square pairs for the band
+        counts = []
+        for a, b in sizes:
+            lay, jobs = L.lvs_plan_pair(a, b, eq_lookups, band)
+            c = [0] * lay["steps"]
+            for j in jobs:
+                c[j["step"]] += 1
+            counts.append(c)
+        longest = max(len(c) for c in counts)
+        waves = {}
+        for w in (0, wave):
+            launch_of, nl = L.lvs_plan_batch(sizes, eq_lookups, band, w)
+            assert nl == longest
+            per_launch = [0] * nl
+            for c, lo in zip(counts, launch_of):
+                assert len(lo) == len(c)
+                assert all(0 <= t < nl for t in lo)
+                assert all(x < y for x, y in zip(lo, lo[1:]))
+                for s, t in enumerate(lo):
+                    per_launch[t] += c[s]
+            assert sum(per_launch) == sum(map(sum, counts))
+            if w == 0:
+                assert all(lo == list(range(len(lo))) for lo in launch_of)
+            waves[w] = sum(-(-j // wave) for j in per_launch)
+        assert waves[wave] <= waves[0]
+
+
+def test_batch_schedule_argument_errors():
+    with pytest.raises(L.LvsError):
+        L.lvs_plan_batch([(3, 4)], 3)
