@@ -107,6 +107,11 @@ def pbs_per_cell(cfg):
     return {1: 3, 2: 3, 3: 1, 4: 2}[cfg]
 
 
+def key_row_bytes(params):
+    """Bytes of one NTT-domain BSK row (one CMux): 3 primes x (k+1)^2 l_b polynomials x N residues x 4 B."""
+    return 3 * (params.k + 1) ** 2 * params.pbs_level * params.N * 4
+
+
 def modmul_per_pbs(p):
     """Algorithmic modular multiplications of one blind rotation on the exact
     NTT path: n * P * [((k+1) l + (k+1)) (N/2) log2 N + (k+1)^2 l N]
@@ -428,6 +433,7 @@ def run_lvs(args):
     mul_lo, mul_hi = L.lvs_probe_int_mul(local)
     modmul_per_sm_clk = 1.0 / (2.0 / mul_lo + 1.0 / mul_hi)
     shoup_stream, bfly_stream = L.lvs_probe_modmul(local)
+    wide_mac, l2_bytes_clk = L.lvs_probe_key_product(local)
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak = n_sms * modmul_per_sm_clk * sm_mhz_max * 1e6 / 1e12
     peak_mul32 = n_sms * MUL32_PER_SM_CLK * sm_mhz_max * 1e6 / 1e12
@@ -556,7 +562,15 @@ def run_lvs(args):
                              if achieved else None,
                              "note": "lvs_probe_modmul: register-resident streams of Shoup products and of complete "
                                      "lazy NTT butterflies (the kernel's form), one CTA per SM; what a kernel made "
-                                     "of these operations can reach, below the multiply issue rates of the peak"}},
+                                     "of these operations can reach, below the multiply issue rates of the peak",
+                             "key_product": {
+                                 "wide_mac_per_sm_clk": wide_mac,
+                                 "l2_read_bytes_per_sm_clk": l2_bytes_clk,
+                                 "key_row_bytes": key_row_bytes(params),
+                                 "key_row_l2_cycles": key_row_bytes(params) / l2_bytes_clk if l2_bytes_clk else None,
+                                 "note": "lvs_probe_key_product: 32x32->64 multiply-accumulates and L2->SM reads in "
+                                         "the key product's shape; one BSK row per CMux per SM read within the "
+                                         "product costs at least key_row_l2_cycles SM cycles"}}},
             "kernels": {"blind_rotate": br, "keyswitch": ks,
                         "ks_plans": {"note": "launch size bucket end -> [PBS per CTA, split] (lvs_ctx_autotune)",
                                      "plans": ks_plans},

@@ -554,6 +554,17 @@ lvs_status lvs_probe_int_mul(int device, double *lo_per_sm_clk, double *hi_per_s
  * the multiply issue rates of lvs_probe_int_mul.  Synchronous; allocates and
  * frees its own small buffers.  LVS_ERR_CUDA without a usable device. */
 lvs_status lvs_probe_modmul(int device, double *shoup_per_sm_clk, double *butterfly_per_sm_clk);
+/* Ceilings of the blind rotation's key product on `device` (no counterpart in
+ * the paper; a measurement aid for the pointwise products of Section 2.2's
+ * external product in the NTT domain): 32x32 -> 64-bit multiply-accumulates per
+ * SM per clock (the Montgomery sums), and L2 -> SM read bytes per SM per clock
+ * in the product's access shape (one CTA of 384 threads per SM, each thread 32
+ * bytes of each of the 16 chunks of a 192 KB key row, all SMs on the same row,
+ * a 96 MB buffer that stays in L2).  Timed with the SM clock counter; each
+ * kernel runs twice and the second run counts.  Synchronous; allocates and frees
+ * its own buffers (96 MB).  LVS_ERR_CUDA without a usable device, LVS_ERR_OOM if
+ * the buffers cannot be allocated. */
+lvs_status lvs_probe_key_product(int device, double *wide_per_sm_clk, double *l2_bytes_per_sm_clk);
 
 /* Key switch + modulus switch only: d_out receives count * (n+1) uint32
  * values round(a * 2N / 2^64) of the key-switched ciphertexts. */

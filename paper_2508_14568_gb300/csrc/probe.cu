@@ -106,6 +106,59 @@ __global__ void __launch_bounds__(kModThreads) k_probe_modmul(uint32_t *out, lon
     if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// Ceilings of the blind rotation's key product.  MODE 0: 32x32 -> 64-bit
+// multiply-accumulates (the Montgomery sums of the key product), 16 independent
+// accumulators per thread.  MODE 1: L2 -> SM reads in the key product's shape:
+// 384 threads, each reading its 32 bytes (two 16-byte loads) of each of the 16
+// chunks of a 192 KB row, all CTAs on the same row at the same time, rows in
+// order through a buffer that stays in L2.  One CTA per SM; thread 0 times the
+// loop with the SM clock counter between barriers.
+constexpr int kKpThreads = 384;
+constexpr int kKpWideIters = 2048;
+constexpr int kKpRows = 500;                             // 500 x 192 KB = 96 MB < L2
+constexpr int kKpRowU4 = 16 * kKpThreads * 2;            // uint4 per row
+constexpr int kKpRowReads = 1000;
+
+template <int MODE>
+__global__ void __launch_bounds__(kKpThreads, 1)
+k_probe_keyprod(const uint4 *__restrict__ rows, uint32_t *out, long long *cycles, uint32_t seed)
+{
+    const int tid = threadIdx.x;
+    uint32_t s = 0;
+    __syncthreads();
+    const long long t0 = clock64();
+    if (MODE == 0) {
+        uint64_t acc[16];
+        uint32_t a[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) { acc[i] = tid + i; a[i] = seed + tid * 7u + i * 13u; }
+        const uint32_t b = seed | 1u;
+#pragma unroll 1
+        for (int it = 0; it < kKpWideIters; ++it) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] += (uint64_t)a[i] * b;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) a[i] = dev::opaque(a[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) s ^= (uint32_t)acc[i] ^ (uint32_t)(acc[i] >> 32);
+    } else {
+#pragma unroll 1
+        for (int it = 0; it < kKpRowReads; ++it) {
+            const uint4 *kp = rows + (size_t)(it % kKpRows) * kKpRowU4 + tid * 2;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const uint4 x = __ldg(kp + q * kKpThreads * 2), y = __ldg(kp + q * kKpThreads * 2 + 1);
+                s += x.x ^ x.y ^ x.z ^ x.w ^ y.x ^ y.y ^ y.z ^ y.w;
+            }
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    out[(size_t)blockIdx.x * kKpThreads + tid] = s;
+    if (tid == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 }  // namespace lvs
 
 using namespace lvs;
@@ -209,5 +262,54 @@ extern "C" lvs_status lvs_probe_int_mul(int device, double *lo_per_sm_clk, doubl
     if (e != cudaSuccess) return cuda_error(e, "lvs_probe_int_mul");
     *lo_per_sm_clk = rate[0];
     *hi_per_sm_clk = rate[1];
+    return LVS_OK;
+}
+
+extern "C" lvs_status lvs_probe_key_product(int device, double *wide_per_sm_clk, double *l2_bytes_per_sm_clk)
+{
+    if (!wide_per_sm_clk || !l2_bytes_per_sm_clk) return set_error(LVS_ERR_ARG, "lvs_probe_key_product: NULL argument");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return set_error(LVS_ERR_CUDA, "lvs_probe_key_product: no such CUDA device");
+    }
+    LVS_CUDA(cudaSetDevice(device));
+    int sms = 0;
+    LVS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    uint32_t *out = nullptr;
+    long long *cyc = nullptr;
+    uint4 *rows = nullptr;
+    const size_t row_bytes = (size_t)kKpRows * kKpRowU4 * sizeof(uint4);
+    if (cudaMalloc((void **)&out, (size_t)sms * kKpThreads * 4) != cudaSuccess ||
+        cudaMalloc((void **)&cyc, (size_t)sms * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc((void **)&rows, row_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(out);
+        cudaFree(cyc);
+        return set_error(LVS_ERR_OOM, "lvs_probe_key_product: device allocation failed");
+    }
+    cudaError_t e = cudaMemset(rows, 0x5a, row_bytes);
+    double rate[2] = {0, 0};
+    std::vector<long long> h(sms);
+    void (*kern[2])(const uint4 *, uint32_t *, long long *, uint32_t) = {k_probe_keyprod<0>, k_probe_keyprod<1>};
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first run warms up (and fills L2)
+            kern[v]<<<sms, kKpThreads>>>(rows, out, cyc, 5u + rep);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpy(h.data(), cyc, sms * sizeof(long long), cudaMemcpyDeviceToHost);
+        }
+        if (e == cudaSuccess) {
+            std::sort(h.begin(), h.end());
+            const double work = v == 0 ? (double)kKpThreads * kKpWideIters * 16       // multiply-accumulates
+                                       : (double)kKpRowReads * kKpRowU4 * sizeof(uint4);   // bytes
+            rate[v] = work / (double)h[sms / 2];
+        }
+    }
+    cudaFree(out);
+    cudaFree(cyc);
+    cudaFree(rows);
+    if (e != cudaSuccess) return cuda_error(e, "lvs_probe_key_product");
+    *wide_per_sm_clk = rate[0];
+    *l2_bytes_per_sm_clk = rate[1];
     return LVS_OK;
 }

@@ -39,6 +39,7 @@ EXPORTS = [
     "lvs_ctx_launch_count", "lvs_ct_string_upload", "lvs_pbs_batch_device_noalloc",
     "lvs_ctx_prepare_fft64", "lvs_pbs_batch_device_fft64", "lvs_noise_budget", "lvs_noise_plan",
     "lvs_ctx_autotune", "lvs_ctx_ks_plan", "lvs_ctx_set_ks_plan", "lvs_probe_int_mul", "lvs_probe_modmul",
+    "lvs_probe_key_product",
     "lvs_preprocess_batch",
     "lvs_ct_string_pin", "lvs_ctx_br_split", "lvs_ctx_set_br_split", "lvs_ctx_set_wave_fill", "lvs_ctx_wave_fill",
     "lvs_plan_batch",
@@ -173,6 +174,7 @@ def _declare(L):
         "lvs_ctx_wave_fill": ([vp, ctypes.POINTER(i32)], i32),
         "lvs_plan_batch": ([szp, szp, sz, u32, i32, sz, ctypes.POINTER(ctypes.c_int64), szp, szp], i32),
         "lvs_probe_modmul": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
+        "lvs_probe_key_product": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
         "lvs_probe_int_mul": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
         "lvs_ctx_ks_plan": ([vp, sz, ctypes.POINTER(i32), ctypes.POINTER(i32)], i32),
         "lvs_ctx_set_ks_plan": ([vp, sz, i32, i32], i32),
@@ -678,6 +680,14 @@ def lvs_probe_modmul(device=0):
     """(Shoup products, lazy NTT butterflies) per SM per clock, measured."""
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib().lvs_probe_modmul(device, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def lvs_probe_key_product(device=0):
+    """(64-bit multiply-accumulates, L2 -> SM bytes in the key product's shape)
+    per SM per clock, measured."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().lvs_probe_key_product(device, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
 
 

@@ -93,6 +93,18 @@ def test_modmul_probe_below_the_multiply_issue_rates():
     assert shoup <= bound * 1.05
 
 
+def test_key_product_probe_plausible():
+    """The key product's ceilings: 64-bit multiply-accumulates no faster than
+    the high-half multiply issue rate (both are double-width products on the
+    multiply pipe, 10% slack for timing), and L2 -> SM bytes per SM per clock
+    positive and below what 384 threads with 32 bytes each could move per clock
+    if every load returned at once (12 KB)."""
+    lo, hi = L.lvs_probe_int_mul(0)
+    wide, l2 = L.lvs_probe_key_product(0)
+    assert 1.0 <= wide <= hi * 1.1
+    assert 1.0 <= l2 <= 384 * 32
+
+
 @pytest.mark.parametrize("which", ["test", "default"])
 def test_three_cta_blind_rotation_bit_exact(which):
     """The blind rotation split over a cluster of three CTAs (one per NTT
