@@ -248,6 +248,9 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
             ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 16 * T * 8, buf, crt + g * 2 * N, tau,
                                    g, twf, twi);
             __syncthreads();
+            // four reconstructions in flight per thread (Garner's steps are a
+            // dependent chain; 2, 6, 8 and 11 measured slower)
+#pragma unroll 4
             for (int c = tid; c < 2 * N; c += NT) {
                 const int j = c >> LOGN, e = c & (N - 1);
                 const uint64_t x = crt3(crt[(0 * 2 + j) * N + e], crt[(1 * 2 + j) * N + e],
