@@ -701,9 +701,11 @@ def run_serving(args):
 
 
 def run_pbs_variants(args):
-    """PBS/s of the two blind-rotation variants on one batch of independent
-    PBS at the default parameters (inputs resident on the device, identity
-    table), with a decryption check of every output."""
+    """PBS/s of the blind-rotation variants (exact NTT with the key read from
+    global memory, the same with the head of each key row staged by bulk copy,
+    FP64 FFT) on one batch of independent PBS at the default parameters (inputs
+    resident on the device, identity table), with a decryption check of every
+    output and the staged outputs compared bit for bit with the default form."""
     import numpy as np
     import torch
     from paper_2508_14568_gb300 import lvs as L
@@ -725,7 +727,16 @@ def run_pbs_variants(args):
             "params": "n=834 k=1 N=2048 pbs 2x2^13 ks 5x2^3", "variants": {}}
     clocks = ClockSampler(0)
     clocks.start()
-    for name, fn in (("ntt_exact", L.lvs_pbs_batch_device), ("fft64", L.lvs_pbs_batch_device_fft64)):
+    def staged(*a):
+        L.lvs_ctx_set_key_staging(ctx, True)
+        try:
+            L.lvs_pbs_batch_device(*a)
+        finally:
+            L.lvs_ctx_set_key_staging(ctx, False)
+
+    ref = None
+    for name, fn in (("ntt_exact", L.lvs_pbs_batch_device), ("ntt_exact_key_staged", staged),
+                     ("fft64", L.lvs_pbs_batch_device_fft64)):
         for _ in range(max(1, args.warmup)):
             fn(ctx, d_in, big + 1, luts, d_out, big + 1, count)
         torch.cuda.synchronize()
@@ -737,8 +748,13 @@ def run_pbs_variants(args):
         ev1.record(stream)
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / args.steps
+        out = d_out.cpu().numpy()
         line["variants"][name] = {"value": count / (ms * 1e-3), "ms_per_batch": ms,
                                   "decrypt_ok": bool(np.array_equal(np.array(got), msgs))}
+        if name == "ntt_exact":
+            ref = out
+        elif name == "ntt_exact_key_staged":
+            line["variants"][name]["bit_equal_to_ntt_exact"] = bool(np.array_equal(out, ref))
     line["clocks"] = clocks.stop()
     L.lvs_ctx_free(ctx)
     print(json.dumps(line), flush=True)

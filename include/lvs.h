@@ -513,6 +513,19 @@ lvs_status lvs_ctx_set_br_split(lvs_ctx *ctx, size_t max_jobs);
  * never a result: every pair's steps keep their order. */
 lvs_status lvs_ctx_set_wave_fill(lvs_ctx *ctx, int32_t enable);
 lvs_status lvs_ctx_wave_fill(lvs_ctx *ctx, int32_t *enabled);
+/* Blind-rotation key source (no counterpart in the paper; Section 2.2's external
+ * product reads one bootstrapping-key row per CMux).  0 (default): every chunk of
+ * a row is read from global memory (L2) by the threads that use it.  1: the
+ * key-staged form: the first three of the 16 chunks of the next CMux's row (36
+ * KB) are copied into shared memory by the TMA engine (`cp.async.bulk`, one 1 KB
+ * copy per warp and chunk, completed on an mbarrier) while the current CMux runs;
+ * the rest come from global memory.  Same results bit for bit; the staged form
+ * measured slower on GB300 and is kept as a measured alternative.  Its waits are
+ * bounded (about one second): if one gives up, the launch's results are void and
+ * the next lvs_ctx_synchronize (or result read) returns LVS_ERR_TIMEOUT; the
+ * context stays usable.  Takes the context lock. */
+lvs_status lvs_ctx_set_key_staging(lvs_ctx *ctx, int32_t enable);
+lvs_status lvs_ctx_key_staging(lvs_ctx *ctx, int32_t *enabled);
 /* Key-switch launches of at least min_jobs PBS run as a dense product on the
  * tensor cores: digits (|d| <= 4) times the key-switching key split into its
  * eight bytes, one bf16 x bf16 -> fp32 product over the whole reduction
@@ -537,6 +550,13 @@ lvs_status lvs_ctx_set_max_launch_jobs(lvs_ctx *ctx, size_t max_jobs);
  * Lets the error paths (batch calls, server admission) be tested without
  * exhausting or faulting a GPU. */
 void lvs_debug_fail_allocations(int32_t count);
+/* Test hook (no counterpart in the paper): with `enable`, the key-staged blind
+ * rotation (lvs_ctx_set_key_staging) never issues warp 0's copies into its first
+ * staging slot, so that slot's first bounded wait runs out (about one second per
+ * launch): the launch's results are void and the next lvs_ctx_synchronize
+ * returns LVS_ERR_TIMEOUT, with no GPU fault and the context still usable.
+ * 0 restores normal copies.  Takes the context lock. */
+lvs_status lvs_debug_drop_key_copy(lvs_ctx *ctx, int32_t enable);
 
 /* Measured issue rate of 32-bit integer multiplies on `device`: low-half
  * (mul.lo / IMAD) and high-half (mul.hi) results per SM per clock, from one

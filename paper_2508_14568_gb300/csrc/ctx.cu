@@ -67,6 +67,50 @@ lvs_status ensure_scratch(lvs_ctx *ctx, size_t njobs_total, size_t njobs_step)
     return LVS_OK;
 }
 
+namespace {
+std::mutex g_fault_mu;
+uint32_t *g_fault_host[64];
+uint32_t *g_fault_dev[64];
+}  // namespace
+
+uint32_t *device_fault_word(int device)
+{
+    if (device < 0 || device >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(g_fault_mu);
+    if (!g_fault_dev[device]) {
+        uint32_t *h = nullptr, *d = nullptr;
+        if (cudaHostAlloc((void **)&h, sizeof(uint32_t), cudaHostAllocMapped) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        *h = 0;
+        if (cudaHostGetDevicePointer((void **)&d, h, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeHost(h);
+            return nullptr;
+        }
+        g_fault_host[device] = h;
+        g_fault_dev[device] = d;
+    }
+    return g_fault_dev[device];
+}
+
+lvs_status device_fault_check(int device)
+{
+    if (device < 0 || device >= 64) return LVS_OK;
+    volatile uint32_t *h;
+    {
+        std::lock_guard<std::mutex> lock(g_fault_mu);
+        h = g_fault_host[device];
+    }
+    if (h && *h) {
+        *h = 0;
+        return set_error(LVS_ERR_TIMEOUT, "blind rotation: a key-chunk copy did not land within about one second; "
+                                          "the results of the work since the last check are void");
+    }
+    return LVS_OK;
+}
+
 cudaEvent_t pool_event(lvs_ctx *ctx)
 {
     if (!ctx->timing.pool.empty()) {
@@ -264,6 +308,7 @@ lvs_status lvs_ctx_create(const lvs_server_key *sk, int device, void *stream, lv
     if (e == cudaSuccess) e = prepare_kernels(N);
     if (e != cudaSuccess) return fail(cuda_error(e, "kernel setup"));
     ctx->br_grid = std::max(1, ctx->num_sms * std::max(1, br_blocks_per_sm(N)));
+    ctx->fault_dev = device_fault_word(device);
     // three-CTA blind rotation for launches that leave SMs idle: by default up
     // to one ciphertext per three SMs (lvs_ctx_autotune measures the crossover)
     ctx->br_clusters = br_cluster_capacity(N);
@@ -342,7 +387,7 @@ lvs_status lvs_ctx_synchronize(lvs_ctx *ctx)
     LVS_CUDA(cudaSetDevice(ctx->device));
     LVS_CUDA(cudaStreamSynchronize(ctx->stream));
     reap_graphs(ctx, true);
-    return LVS_OK;
+    return device_fault_check(ctx->device);
 }
 
 lvs_status lvs_ctx_set_timing(lvs_ctx *ctx, int enable)

@@ -27,6 +27,87 @@ __device__ __forceinline__ uint32_t residue_of_signed(int64_t x, uint32_t p)
     return (uint32_t)(r < 0 ? r + p : r);
 }
 
+// NTT-domain key layout: for BSK index i, prime g and register q, the [T][8]
+// words of the T threads (slot = row * 2 + column) are stored warp by warp,
+// each warp's 32 threads as one contiguous kilobyte [half][lane][4 u32]: the
+// word of (tau, slot) is at key_lane_word(tau) + (slot >> 2) * 128 + (slot & 3).
+// A warp's piece is one bulk copy, and both halves read conflict-free.
+__device__ __forceinline__ uint32_t key_lane_word(uint32_t tau) { return (tau >> 5) * 256u + (tau & 31u) * 4u; }
+
+// Bulk copies global -> shared through the TMA engine, completed on an
+// mbarrier (transaction bytes), and bounded waits on the barrier's phase.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *m)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(m))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *m, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(m)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+constexpr long long kKeyWaitCycles = 2000000000LL;   // about one second at the GB300's SM clock
+// Wait for phase `parity` of m.  Gives up after kKeyWaitCycles, or at once when
+// another thread of the CTA has given up (*abort, unless `final`): it then sets
+// *abort and the host-visible *fault, and the caller goes on with whatever the
+// slot holds, so every barrier of the kernel is still reached and the launch
+// ends normally (its results are void; the host reports LVS_ERR_TIMEOUT).
+// `final`: the wait for a copy that is known to be in flight before the CTA
+// exits, which must not be cut short by another thread's give-up.  Returns
+// whether the phase completed.
+__device__ __forceinline__ bool key_wait(uint64_t *m, uint32_t parity, volatile uint32_t *abort,
+                                         volatile uint32_t *fault, bool final = false)
+{
+    if (mbar_test(m, parity)) return true;
+    const long long t0 = clock64();
+    while (final || *abort == 0) {
+        if (mbar_test(m, parity)) return true;
+        if (clock64() - t0 > kKeyWaitCycles) {
+            *abort = 1;
+            if (fault) *fault = 1;
+            return false;
+        }
+    }
+    return false;
+}
+
+// Staging of the head of each BSK row in shared memory (the key-staged form of
+// the blind rotation): KR slots, slot q holding chunk q (register q of the row,
+// 12 KB for the CTA) of the next CMux's row; each warp's kilobyte is its own
+// bulk copy on its own barrier, issued as soon as the warp has used the current
+// row's chunk q, so it lands while the rest of the CMux runs.  Every slot is
+// used once per CMux: the barrier phase of CMux m is m & 1 (r).  drop: a test
+// hook that never issues warp 0's copies into slot 0 (its first wait then runs
+// out and the launch reports LVS_ERR_TIMEOUT).  Once any wait of the CTA has
+// given up, no warp issues another copy (a slot whose copy may still be in
+// flight is never refilled); lane 0 of each warp keeps which of its copies it has
+// not yet seen land (pend, with the barrier parity of each in par) and waits for
+// those before the CTA exits.
+template <int KR>
+struct KeyRing {
+    uint4 *slots;              // [KR][warps][64] uint4
+    uint64_t *mbar;            // [KR][warps]
+    volatile uint32_t *abort;  // shared: set once a wait gave up
+    volatile uint32_t *fault;  // host-visible (mapped), may be null
+    uint32_t r;
+    uint32_t drop;
+    uint32_t pend, par;        // lane 0 of each warp
+};
+
 // Value of the rotated test polynomial v' = X^{-box/2} v, v[t] = f[t / box] * Delta,
 // at index idx in [0, 2N) of X^{-b} v' (negacyclic extension).
 template <int LOGN>
@@ -43,14 +124,20 @@ __device__ __forceinline__ uint64_t test_poly_at(const uint8_t (&f)[16], uint32_
 
 // External product core for prime group g: digit residues d (L0 layout, in
 // [0, p)) -> forward NTT -> Montgomery products with the key slice `key`
-// ([16][T][8] u32 for this prime, this thread at +tau*8) -> inverse NTT ->
+// ([16][T][8] u32 for this prime, key_lane_word layout) -> inverse NTT ->
 // residues of the two output polynomials written to out[j*N + e].
 // OUT_IN_BUF: out lies in this group's exchange buffer, so the group first
 // waits until every thread has read its last inverse exchange.
-template <int LOGN, bool OUT_IN_BUF = false>
+// KR > 0: chunks 0 .. KR-1 of `key` come from the staging slots of R (in flight
+// or landed on entry); after using chunk q < KR the warp refills slot q with
+// chunk q of `key_next` (the next CMux's slice); the other chunks, and the first
+// two of them issued before the slots are read, come from global memory.
+template <int LOGN, bool OUT_IN_BUF = false, int KR = 0>
 __device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][16], const uint32_t *__restrict__ key,
                                                  uint32_t *buf, uint32_t *out, uint32_t tau, int g,
-                                                 const uint2 *__restrict__ twf, const uint2 *__restrict__ twi)
+                                                 const uint2 *__restrict__ twf, const uint2 *__restrict__ twi,
+                                                 KeyRing<KR> *R = nullptr,
+                                                 const uint32_t *__restrict__ key_next = nullptr, int tid = 0)
 {
     using Lay = Layout<LOGN>;
     constexpr int N = Lay::N, T = Lay::T;
@@ -58,15 +145,41 @@ __device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][16], const uin
     ntt_forward4<LOGN>(d, reinterpret_cast<uint4 *>(buf), tau, twf, p, 1 + g, z);
 
     // pointwise: out_c = sum_r D_r * K[r][c] (Montgomery), written over D_0, D_1
-    const uint4 *kp = reinterpret_cast<const uint4 *>(key + (size_t)tau * 8);
-    uint4 ka = __ldg(kp), kb = __ldg(kp + 1);
+    constexpr int NW = 3 * T / 32;   // warps of the CTA (ring)
+    const int w = tid >> 5, lane = tid & 31;
+    const uint4 *kp = reinterpret_cast<const uint4 *>(key + key_lane_word(tau));
+    // chunk q < KR: from slot q, landed during the previous CMux (barrier phase
+    // R->r); the others straight from global memory
+    auto head_load = [&](int q, uint4 &x, uint4 &y) {
+        if (key_wait(R->mbar + q * NW + w, R->r, R->abort, R->fault)) R->pend &= ~(1u << q);
+        const uint4 *sp = R->slots + (size_t)(q * NW + w) * 64;
+        x = sp[lane];
+        y = sp[32 + lane];
+    };
+    uint4 ka, kb, ea, eb, fa, fb;
+    if constexpr (KR > 0) {
+        ea = __ldg(kp + (size_t)KR * T * 2);
+        eb = __ldg(kp + (size_t)KR * T * 2 + 32);
+        fa = __ldg(kp + (size_t)(KR + 1) * T * 2);
+        fb = __ldg(kp + (size_t)(KR + 1) * T * 2 + 32);
+        head_load(0, ka, kb);
+    }
+    else {
+        ka = __ldg(kp);
+        kb = __ldg(kp + 32);
+    }
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         uint4 na, nb;
         if (q + 1 < 16) {
-            const uint4 *np = kp + (size_t)(q + 1) * T * 2;
-            na = __ldg(np);
-            nb = __ldg(np + 1);
+            if (q + 1 < KR) head_load(q + 1, na, nb);
+            else if (KR > 0 && q + 1 == KR) { na = ea; nb = eb; }
+            else if (KR > 0 && q + 1 == KR + 1) { na = fa; nb = fb; }
+            else {
+                const uint4 *np = kp + (size_t)(q + 1) * T * 2;
+                na = __ldg(np);
+                nb = __ldg(np + 32);
+            }
         }
         // transform values in [0, 4p) -> [0, 2p); key residues < p: each sum of
         // four products is below 8 p^2 < 2^63, REDC returns it below 3p, and one
@@ -80,6 +193,18 @@ __device__ __forceinline__ void ext_product_core(uint32_t (&d)[4][16], const uin
         const uint64_t t1 = (uint64_t)d0 * ka.y + (uint64_t)d1 * ka.w + (uint64_t)d2 * kb.y + (uint64_t)d3 * kb.w;
         d[0][q] = csubz(redc(t0, p, pinv), 2 * p, z);
         d[1][q] = csubz(redc(t1, p, pinv), 2 * p, z);
+        if (q < KR) {
+            // every lane has read chunk q (and used it): its slot takes chunk q of
+            // the next CMux
+            __syncwarp();
+            if (lane == 0 && !(R->drop && w == 0 && q == 0) && *R->abort == 0) {
+                fence_proxy_async();
+                bulk_g2s(R->slots + (size_t)(q * NW + w) * 64, key_next + (size_t)q * T * 8 + (tau >> 5) * 256u, 1024,
+                         R->mbar + q * NW + w);
+                R->pend |= 1u << q;   // completes the next CMux's phase
+                R->par = (R->par & ~(1u << q)) | ((R->r ^ 1u) << q);
+            }
+        }
         if (q + 1 < 16) { ka = na; kb = nb; }
     }
     ntt_inverse2<LOGN>(d, reinterpret_cast<uint2 *>(buf), tau, twi, p, 1 + g, z);
@@ -147,9 +272,11 @@ __device__ __forceinline__ void decompose_shared(uint32_t *bufs, const uint64_t 
     for (int c = tid; c < 2 * N; c += nthreads) {
         const int j = c >> LOGN;
         const uint32_t e = c & (N - 1);
+        // (X^a ACC)[e] = +-ACC[(e - a) mod N], negative when (e - a) mod 2N >= N
         const uint32_t src = (e - a) & (2 * N - 1);
-        const uint64_t *A = acc + j * 2 * N;
-        const uint64_t x = A[src] - A[e];
+        const uint64_t *A = acc + j * N;
+        const uint64_t rot = A[src & (N - 1)];
+        const uint64_t x = (src < (uint32_t)N ? rot : 0 - rot) - A[e];
         const uint32_t v = ((uint32_t)(x >> 32) + hround) >> hshift;
         const uint32_t u2 = v & (B - 1);
         const uint32_t c2 = u2 >> (base_log - 1);
@@ -166,14 +293,16 @@ __device__ __forceinline__ void decompose_shared(uint32_t *bufs, const uint64_t 
 // epilogue: a_0 = A[0], a_u = -A[N - u] = A[2N - u] (u > 0), b = B[0]; a cell
 // job updates v[i] = M - h[i-1][j], h[j] = M - v[i][j-1] in place (and copies
 // one of them to its tap row), a store job writes the ciphertext (and its tap).
-template <int LOGN>
+// EXT: acc negacyclically extended ([2][2N]); otherwise stored once ([2][N]).
+template <int LOGN, bool EXT>
 __device__ __forceinline__ void sample_extract_epilogue(const Job &J, const uint64_t *acc, int tid, int nthreads)
 {
     constexpr int N = 1 << LOGN;
     uint64_t *o0 = J.dst[0];
     uint64_t *o1 = J.dst[1];
     for (int u = tid; u <= N; u += nthreads) {
-        const uint64_t val = u == N ? acc[2 * N] : acc[(2 * N - u) & (2 * N - 1)];
+        const uint64_t val = EXT ? (u == N ? acc[2 * N] : acc[(2 * N - u) & (2 * N - 1)])
+                                 : (u == N ? acc[N] : (u == 0 ? acc[0] : 0 - acc[N - u]));
         if (J.kind == JOB_CELL) {
             const uint64_t vold = o0[u], hold = o1[u];
             const uint64_t vn = val - hold, hn = val - vold;
@@ -188,26 +317,38 @@ __device__ __forceinline__ void sample_extract_epilogue(const Job &J, const uint
 }
 
 // ---------------------------------------------------------------- blind rotation
-template <int LOGN>
+// Shared memory of k_blind_rotate: the accumulator (stored once, [2][N]), one
+// exchange buffer per prime group, the three primes' output residues for the
+// CRT and, in the key-staged form (KR > 0), the KR staging slots of 12 KB and
+// their barriers (one per slot and warp) plus the give-up flag.
+constexpr int kKeyStageChunks = 3;   // what fits beside the 182 KB above
+template <int LOGN, int KR>
 struct BrSmem {
     static constexpr int N = 1 << LOGN;
-    static constexpr size_t acc_bytes = 2 * 2 * N * sizeof(uint64_t);   // negacyclically extended
+    static constexpr int NW = 3 * N / 16 / 32;
+    static constexpr size_t acc_bytes = 2 * N * sizeof(uint64_t);
     static constexpr size_t buf_bytes = 3 * (size_t)ExWords<LOGN>::WORDS * 16;
     static constexpr size_t crt_bytes = 3 * 2 * N * sizeof(uint32_t);
-    static constexpr size_t total = acc_bytes + buf_bytes + crt_bytes;
+    static constexpr size_t ring_bytes = (size_t)KR * NW * 1024;
+    static constexpr size_t mbar_bytes = KR > 0 ? (size_t)KR * NW * 8 + 16 : 0;
+    static constexpr size_t ring_off = acc_bytes + buf_bytes + crt_bytes;
+    static constexpr size_t total = ring_off + ring_bytes + mbar_bytes;
 };
 
-template <int LOGN>
+// KR = 0: every key chunk from global memory (L2); KR = kKeyStageChunks: the
+// key-staged form (KeyRing).  drop_copy: KeyRing::drop (tests only).
+template <int LOGN, int KR>
 __global__ void __launch_bounds__(3 * (1 << LOGN) / 16, 1)
 k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__restrict__ ms, uint32_t n, const uint32_t *__restrict__ bsk,
                const uint2 *__restrict__ tw, const uint8_t *__restrict__ luts, int lut_per_job,
-               uint32_t base_log)
+               uint32_t base_log, volatile uint32_t *fault, uint32_t drop_copy)
 {
     using Lay = Layout<LOGN>;
-    constexpr int N = Lay::N, T = Lay::T, NT = 3 * T;
+    using SM = BrSmem<LOGN, KR>;
+    constexpr int N = Lay::N, T = Lay::T, NT = 3 * T, NW = SM::NW;
     extern __shared__ __align__(16) uint8_t smem_raw[];
-    uint64_t *acc = reinterpret_cast<uint64_t *>(smem_raw);
-    uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw + BrSmem<LOGN>::acc_bytes);
+    uint64_t *acc = reinterpret_cast<uint64_t *>(smem_raw);   // [2][N]: mask, body
+    uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw + SM::acc_bytes);
     uint32_t *crt = bufs + 3 * 4 * ExWords<LOGN>::WORDS;
 
     const int tid = threadIdx.x;
@@ -217,6 +358,38 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
     const uint2 *twf = tw + (size_t)(g * 2 + 0) * N;
     const uint2 *twi = tw + (size_t)(g * 2 + 1) * N;
     const size_t key_row = (size_t)3 * 16 * T * 8;   // u32 per BSK index i
+    const uint32_t *bsk_g = bsk + (size_t)g * 16 * T * 8;
+
+    // key staging (KR > 0): the CMux sequence runs through the rows i, i + 1
+    // mod n, ... of every job of this CTA; the slots start with the head of row 0
+    KeyRing<KR> R;
+    const int w = tid >> 5, lane = tid & 31;
+    const bool has_work = blockIdx.x < njobs;
+    if constexpr (KR > 0) {
+        R.slots = reinterpret_cast<uint4 *>(smem_raw + SM::ring_off);
+        R.mbar = reinterpret_cast<uint64_t *>(smem_raw + SM::ring_off + SM::ring_bytes);
+        R.abort = reinterpret_cast<volatile uint32_t *>(R.mbar + KR * NW);
+        R.fault = fault;
+        R.r = 0;
+        R.drop = drop_copy;
+        R.pend = 0;
+        R.par = 0;
+        if (tid == 0) {
+            for (int k = 0; k < KR * NW; ++k) mbar_init(R.mbar + k, 1);
+            *R.abort = 0;
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (has_work && lane == 0) {
+#pragma unroll
+            for (int q = 0; q < KR; ++q)
+                if (!(drop_copy && w == 0 && q == 0)) {
+                    bulk_g2s(R.slots + (size_t)(q * NW + w) * 64, bsk_g + (size_t)q * T * 8 + (tau >> 5) * 256u, 1024,
+                             R.mbar + q * NW + w);
+                    R.pend |= 1u << q;   // phase 0
+                }
+        }
+    }
 
     for (uint32_t job = blockIdx.x; job < njobs; job += gridDim.x) {
         const Job J = jobs[job];
@@ -227,26 +400,30 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
             const uint4 lv = *reinterpret_cast<const uint4 *>(lp);
             memcpy(f, &lv, 16);
         }
-        // ACC = (0, X^{-b} v'), kept negacyclically extended: acc[j][t + N] =
-        // -acc[j][t], so that (X^a ACC)[e] = acc[j][(e - a) mod 2N] is a plain read
+        // ACC = (0, X^{-b} v'), each polynomial stored once (acc[j][e], e < N)
         const uint32_t b = __ldg(msj + n);
-        for (int t = tid; t < 2 * N; t += NT) {
+        for (int t = tid; t < N; t += NT) {
             acc[t] = 0;
-            acc[2 * N + t] = test_poly_at<LOGN>(f, (t + b) & (2 * N - 1));
+            acc[N + t] = test_poly_at<LOGN>(f, (t + b) & (2 * N - 1));
         }
         __syncthreads();
 
         for (uint32_t i = 0; i < n; ++i) {
             const uint32_t a = __ldg(msj + i);
-            if (a == 0) continue;   // X^0 ACC - ACC = 0: the external product is exactly 0
+            // X^0 ACC - ACC = 0: the external product is exactly 0.  The staged
+            // form runs it anyway (digits 0, an exactly zero product) so that
+            // every CMux takes its row's head from the slots in order.
+            if (KR == 0 && a == 0) continue;
+            const uint32_t inext = i + 1 == n ? 0 : i + 1;
             // digits once for the CTA into the exchange buffers; each prime group
             // then loads its positions (the same words its first exchange rewrites)
             decompose_shared<LOGN>(bufs, acc, a, tid, NT, base_log);
             __syncthreads();
             uint32_t d[4][16];
             ld4<Lay::B0, 4>(reinterpret_cast<const uint4 *>(buf), d, w16(Lay::base0(tau)));
-            ext_product_core<LOGN>(d, bsk + (size_t)i * key_row + (size_t)g * 16 * T * 8, buf, crt + g * 2 * N, tau,
-                                   g, twf, twi);
+            ext_product_core<LOGN, false, KR>(d, bsk_g + (size_t)i * key_row, buf, crt + g * 2 * N, tau, g, twf, twi,
+                                              &R, bsk_g + (size_t)inext * key_row, tid);
+            if constexpr (KR > 0) R.r ^= 1u;
             __syncthreads();
             // four reconstructions in flight per thread (Garner's steps are a
             // dependent chain; 2, 6, 8 and 11 measured slower)
@@ -255,16 +432,23 @@ k_blind_rotate(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *__r
                 const int j = c >> LOGN, e = c & (N - 1);
                 const uint64_t x = crt3(crt[(0 * 2 + j) * N + e], crt[(1 * 2 + j) * N + e],
                                         crt[(2 * 2 + j) * N + e], c_pc);
-                uint64_t *A = acc + j * 2 * N;
-                const uint64_t y = A[e] + x;
-                A[e] = y;
-                A[e + N] = 0 - y;
+                acc[j * N + e] += x;
             }
             __syncthreads();
         }
 
-        sample_extract_epilogue<LOGN>(J, acc, tid, NT);
+        sample_extract_epilogue<LOGN, false>(J, acc, tid, NT);
         __syncthreads();
+    }
+    // no bulk copy may be in flight when the CTA exits: lane 0 of each warp
+    // waits for the copies it has not seen land (normally its last KR, the head
+    // of row 0 again, never used)
+    if constexpr (KR > 0) {
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < KR; ++k)
+                if (R.pend & (1u << k)) key_wait(R.mbar + k * NW + w, (R.par >> k) & 1u, R.abort, R.fault, true);
+        }
     }
 }
 
@@ -422,7 +606,7 @@ __global__ void k_ksk_colsum(const uint64_t *__restrict__ ksk, uint32_t rows, ui
 
 // ---------------------------------------------------------------- key conversion
 // BSK (coefficient domain, [i][row][col][N] u64) -> NTT domain
-// out[i][g][q][tau][slot = row*2+col] = NTT_p(row,col)[pos(tau,q)] * R * N^{-1} mod p
+// out[i][g][q][(tau, slot = row*2+col) in key_lane_word order] = NTT_p(row,col)[pos(tau,q)] * R * N^{-1} mod p
 template <int LOGN>
 __global__ void __launch_bounds__(3 * (1 << LOGN) / 16)
 k_bsk_to_ntt(const uint64_t *__restrict__ coef, uint32_t count, uint32_t *__restrict__ out,
@@ -452,7 +636,7 @@ k_bsk_to_ntt(const uint64_t *__restrict__ coef, uint32_t count, uint32_t *__rest
     ntt_forward4<LOGN>(v, reinterpret_cast<uint4 *>(bufs + g * 4 * ExWords<LOGN>::WORDS), tau, tw + (size_t)(g * 2) * N,
                        p, 1 + g, c_pc.zero);
     const uint32_t m = g == 0 ? m0 : (g == 1 ? m1 : m2), msh = g == 0 ? ms0 : (g == 1 ? ms1 : ms2);
-    uint32_t *dst = out + (size_t)i * 3 * 16 * T * 8 + (size_t)g * 16 * T * 8 + (size_t)tau * 8 + 4 * h;
+    uint32_t *dst = out + (size_t)i * 3 * 16 * T * 8 + (size_t)g * 16 * T * 8 + key_lane_word(tau) + 128 * h;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
 #pragma unroll
@@ -550,7 +734,7 @@ k_blind_rotate_cl(const Job *__restrict__ jobs, uint32_t njobs, const uint32_t *
             }
             cl.sync();   // every copy of the accumulator is updated; residues may be overwritten
         }
-        if (g == 0) sample_extract_epilogue<LOGN>(J, acc, (int)tau, T);
+        if (g == 0) sample_extract_epilogue<LOGN, true>(J, acc, (int)tau, T);
         __syncthreads();
     }
 }
@@ -564,7 +748,7 @@ k_poly_mul(const int32_t *__restrict__ dig, const uint32_t *__restrict__ keyntt,
     using Lay = Layout<LOGN>;
     constexpr int N = Lay::N, T = Lay::T, NT = 3 * T;
     extern __shared__ __align__(16) uint8_t smem_raw[];
-    uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw + BrSmem<LOGN>::acc_bytes);
+    uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw + BrSmem<LOGN, 0>::acc_bytes);
     uint32_t *crt = bufs + 3 * 4 * ExWords<LOGN>::WORDS;
     const int tid = threadIdx.x, g = tid / T;
     const uint32_t tau = tid % T;
@@ -607,7 +791,7 @@ __global__ void k_fill_trivial(uint64_t *arena, size_t stride, uint32_t big, siz
 using namespace dev;
 
 int br_threads(uint32_t N) { return 3 * (int)N / 16; }
-int br_smem_bytes(uint32_t N) { return N == 2048 ? (int)BrSmem<11>::total : (int)BrSmem<9>::total; }
+int br_smem_bytes(uint32_t N) { return N == 2048 ? (int)BrSmem<11, 0>::total : (int)BrSmem<9, 0>::total; }
 size_t bsk_ntt_words(uint32_t n, uint32_t N) { return (size_t)n * 3 * 16 * (N / 16) * 8; }
 
 cudaError_t upload_prime_consts(const PrimeConsts &pc) { return cudaMemcpyToSymbol(c_pc, &pc, sizeof(pc)); }
@@ -615,11 +799,14 @@ cudaError_t upload_prime_consts(const PrimeConsts &pc) { return cudaMemcpyToSymb
 template <int LOGN>
 static cudaError_t set_attrs()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_blind_rotate<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)BrSmem<LOGN>::total);
+    cudaError_t e = cudaFuncSetAttribute(k_blind_rotate<LOGN, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)BrSmem<LOGN, 0>::total);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_blind_rotate<LOGN, kKeyStageChunks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BrSmem<LOGN, kKeyStageChunks>::total);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_poly_mul<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)BrSmem<LOGN>::total);
+                             (int)BrSmem<LOGN, 0>::total);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_blind_rotate_cl<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)BrClSmem<LOGN>::total);
@@ -658,8 +845,8 @@ int br_blocks_per_sm(uint32_t N)
 {
     int nb = 0;
     cudaError_t e = N == 2048
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate<11>, br_threads(N), BrSmem<11>::total)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate<9>, br_threads(N), BrSmem<9>::total);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate<11, 0>, br_threads(N), BrSmem<11, 0>::total)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blind_rotate<9, 0>, br_threads(N), BrSmem<9, 0>::total);
     if (e != cudaSuccess) { cudaGetLastError(); return 1; }
     return nb;
 }
@@ -755,12 +942,23 @@ cudaError_t launch_blind_rotate(const lvs_ctx *ctx, const Job *jobs, size_t njob
         return cudaGetLastError();
     }
     const unsigned grid = (unsigned)std::min<size_t>(njobs, (size_t)ctx->br_grid);
-    if (p.N == 2048)
-        k_blind_rotate<11><<<grid, br_threads(p.N), BrSmem<11>::total, s>>>(
-            jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log);
-    else
-        k_blind_rotate<9><<<grid, br_threads(p.N), BrSmem<9>::total, s>>>(
-            jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log);
+    const uint32_t drop = ctx->debug_drop_key_copy ? 1u : 0u;
+    constexpr int KS = kKeyStageChunks;
+    if (p.N == 2048) {
+        if (ctx->key_staging)
+            k_blind_rotate<11, KS><<<grid, br_threads(p.N), BrSmem<11, KS>::total, s>>>(
+                jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log, ctx->fault_dev, drop);
+        else
+            k_blind_rotate<11, 0><<<grid, br_threads(p.N), BrSmem<11, 0>::total, s>>>(
+                jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log, ctx->fault_dev, 0u);
+    } else {
+        if (ctx->key_staging)
+            k_blind_rotate<9, KS><<<grid, br_threads(p.N), BrSmem<9, KS>::total, s>>>(
+                jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log, ctx->fault_dev, drop);
+        else
+            k_blind_rotate<9, 0><<<grid, br_threads(p.N), BrSmem<9, 0>::total, s>>>(
+                jobs, (uint32_t)njobs, ms, p.n, ctx->bsk_ntt, t2, luts, lut_per_job, p.pbs_base_log, ctx->fault_dev, 0u);
+    }
     return cudaGetLastError();
 }
 
@@ -779,9 +977,9 @@ cudaError_t launch_poly_mul(const lvs_ctx *ctx, const int32_t *dig, const uint32
     const uint32_t N = ctx->P.p.N;
     const uint2 *t2 = reinterpret_cast<const uint2 *>(ctx->tw);
     if (N == 2048)
-        k_poly_mul<11><<<(unsigned)count, br_threads(N), BrSmem<11>::total, s>>>(dig, keyntt, out, (uint32_t)count, t2);
+        k_poly_mul<11><<<(unsigned)count, br_threads(N), BrSmem<11, 0>::total, s>>>(dig, keyntt, out, (uint32_t)count, t2);
     else
-        k_poly_mul<9><<<(unsigned)count, br_threads(N), BrSmem<9>::total, s>>>(dig, keyntt, out, (uint32_t)count, t2);
+        k_poly_mul<9><<<(unsigned)count, br_threads(N), BrSmem<9, 0>::total, s>>>(dig, keyntt, out, (uint32_t)count, t2);
     return cudaGetLastError();
 }
 

@@ -141,7 +141,10 @@ struct lvs_ctx {
     int br_clusters = 0;           // resident clusters of the three-CTA blind rotation
     size_t br_split_max = 0;       // launches of at most this many PBS use it (0: never)
     // device keys
-    uint32_t *bsk_ntt = nullptr;   // [n][kPrimes][16][T][8] u32
+    uint32_t *bsk_ntt = nullptr;   // [n][kPrimes][16][q][key_lane_word order] u32
+    uint32_t *fault_dev = nullptr; // device view of this device's give-up word (device_fault_word)
+    int key_staging = 0;           // 1: key-staged blind rotation (head of each BSK row by bulk copy)
+    bool debug_drop_key_copy = false; // tests: the staged form never issues one warp's copies
     uint64_t *ksk = nullptr;       // [kN][ks_l][n+1]
     uint64_t *ksk_colsum = nullptr; // [n+1]: column sums of the KSK
     uint32_t *tw = nullptr;        // twiddles: uint2 {w, w_shoup} [prime][fwd, inv][N]
@@ -227,6 +230,12 @@ int br_smem_bytes(uint32_t N);
 int br_cluster_capacity(uint32_t N);
 int br_threads(uint32_t N);
 size_t bsk_ntt_words(uint32_t n, uint32_t N);
+// Per-device word in mapped pinned host memory that a kernel sets when one of
+// its bounded device-side waits gives up (allocated once per device, kept for
+// the life of the process); device_fault_check reads and clears it:
+// LVS_ERR_TIMEOUT if it was set.  Call after the work has been synchronized.
+uint32_t *device_fault_word(int device);
+lvs_status device_fault_check(int device);
 
 // host tables (tables.cu)
 void make_twiddles(uint32_t N, std::vector<uint32_t> &out);

@@ -866,6 +866,7 @@ lvs_status lvs_result_export(const lvs_result *r, size_t pair, uint64_t *dst, si
         if (*words < it.count * w) return set_error(LVS_ERR_ARG, "lvs_result_export: destination too small");
         LVS_CUDA(cudaSetDevice(r->device));
         LVS_CUDA(cudaEventSynchronize(r->done));
+        if (lvs_status st = device_fault_check(r->device); st != LVS_OK) return st;
         if (it.count)
             LVS_CUDA(cudaMemcpy2D(dst, w * 8, r->d + it.first * r->stride, r->stride * 8, w * 8, it.count,
                                   cudaMemcpyDeviceToHost));
@@ -942,6 +943,7 @@ lvs_status lvs_decrypt_all(const lvs_client_key *ck, const lvs_result *r, uint32
     std::vector<uint64_t> host(total * w);
     LVS_CUDA(cudaSetDevice(r->device));
     LVS_CUDA(cudaEventSynchronize(r->done));
+    if (lvs_status st = device_fault_check(r->device); st != LVS_OK) return st;
     if (total)
         LVS_CUDA(cudaMemcpy2D(host.data(), w * 8, r->d, r->stride * 8, w * 8, total, cudaMemcpyDeviceToHost));
     for (size_t p = 0; p < r->items.size(); ++p) {

@@ -230,6 +230,7 @@ void worker_loop(lvs_server *S)
             if (st == LVS_OK) {
                 const cudaError_t e = cudaStreamSynchronize(ctx->stream);
                 if (e != cudaSuccess) st = cuda_error(e, "server step");
+                else st = device_fault_check(ctx->device);
             }
         }
         const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -248,6 +248,30 @@ lvs_status lvs_ctx_wave_fill(lvs_ctx *ctx, int32_t *enabled)
     return LVS_OK;
 }
 
+lvs_status lvs_ctx_set_key_staging(lvs_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return set_error(LVS_ERR_ARG, "lvs_ctx_set_key_staging: NULL context");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->key_staging = enable != 0 ? 1 : 0;
+    return LVS_OK;
+}
+
+lvs_status lvs_ctx_key_staging(lvs_ctx *ctx, int32_t *enabled)
+{
+    if (!ctx || !enabled) return set_error(LVS_ERR_ARG, "lvs_ctx_key_staging: NULL argument");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    *enabled = ctx->key_staging;
+    return LVS_OK;
+}
+
+lvs_status lvs_debug_drop_key_copy(lvs_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return set_error(LVS_ERR_ARG, "lvs_debug_drop_key_copy: NULL context");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->debug_drop_key_copy = enable != 0;
+    return LVS_OK;
+}
+
 lvs_status lvs_ctx_br_split(lvs_ctx *ctx, size_t *max_jobs)
 {
     if (!ctx || !max_jobs) return set_error(LVS_ERR_ARG, "lvs_ctx_br_split: NULL argument");

@@ -39,7 +39,7 @@ EXPORTS = [
     "lvs_ctx_launch_count", "lvs_ct_string_upload", "lvs_pbs_batch_device_noalloc",
     "lvs_ctx_prepare_fft64", "lvs_pbs_batch_device_fft64", "lvs_noise_budget", "lvs_noise_plan",
     "lvs_ctx_autotune", "lvs_ctx_ks_plan", "lvs_ctx_set_ks_plan", "lvs_probe_int_mul", "lvs_probe_modmul",
-    "lvs_probe_key_product",
+    "lvs_probe_key_product", "lvs_ctx_set_key_staging", "lvs_ctx_key_staging", "lvs_debug_drop_key_copy",
     "lvs_preprocess_batch",
     "lvs_ct_string_pin", "lvs_ctx_br_split", "lvs_ctx_set_br_split", "lvs_ctx_set_wave_fill", "lvs_ctx_wave_fill",
     "lvs_plan_batch",
@@ -171,6 +171,9 @@ def _declare(L):
         "lvs_ctx_set_br_split": ([vp, sz], i32),
         "lvs_preprocess_batch": ([vp, vpp, sz, ctypes.c_char_p, sz, vpp], i32),
         "lvs_ctx_set_wave_fill": ([vp, i32], i32),
+        "lvs_ctx_set_key_staging": ([vp, i32], i32),
+        "lvs_ctx_key_staging": ([vp, ctypes.POINTER(i32)], i32),
+        "lvs_debug_drop_key_copy": ([vp, i32], i32),
         "lvs_ctx_wave_fill": ([vp, ctypes.POINTER(i32)], i32),
         "lvs_plan_batch": ([szp, szp, sz, u32, i32, sz, ctypes.POINTER(ctypes.c_int64), szp, szp], i32),
         "lvs_probe_modmul": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
@@ -370,6 +373,20 @@ def lvs_ctx_wave_fill(ctx):
     v = ctypes.c_int32()
     _check(lib().lvs_ctx_wave_fill(ctx, ctypes.byref(v)))
     return bool(v.value)
+
+
+def lvs_ctx_set_key_staging(ctx, enable):
+    _check(lib().lvs_ctx_set_key_staging(ctx, 1 if enable else 0))
+
+
+def lvs_ctx_key_staging(ctx):
+    v = ctypes.c_int32()
+    _check(lib().lvs_ctx_key_staging(ctx, ctypes.byref(v)))
+    return bool(v.value)
+
+
+def lvs_debug_drop_key_copy(ctx, enable):
+    _check(lib().lvs_debug_drop_key_copy(ctx, 1 if enable else 0))
 
 
 def lvs_plan_table(m, alphabet, subset):

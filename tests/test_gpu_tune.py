@@ -211,3 +211,75 @@ def test_autotune_sets_keyswitch_gemm_threshold(full):
     ck, ctx, K = full
     L.lvs_ctx_autotune(ctx)
     assert L.lvs_ctx_ks_gemm_min(ctx) in (0, 256, 1024, 4096)
+
+
+@pytest.mark.parametrize("which", ["test", "default"])
+def test_key_staged_blind_rotation_bit_exact(which):
+    """The key-staged blind rotation (the head of each bootstrapping-key row
+    copied into shared memory by bulk copies during the previous CMux) gives
+    the same ciphertexts as the default form, over several jobs per CTA (the
+    staging runs across job boundaries), and the oracle's: every output at the
+    test parameters, a sample of both waves at the full parameters."""
+    params, oparams = (L.lvs_params_test(), T.params_test()) if which == "test" else \
+        (L.lvs_params_default(), T.params_lvs())
+    ck, sk = L.lvs_keygen(params, 8)
+    ctx = L.lvs_ctx_create(sk, 0)
+    K = T.Keys(oparams, 8)
+    big = K.big_dim
+    count = 700 if which == "test" else 170
+    rng = np.random.default_rng(19)
+    msgs = rng.integers(0, 32, size=count)
+    luts = rng.integers(0, 32, size=(count, 16), dtype=np.uint8)
+    cts = np.stack([T.encrypt(K, int(m), 17, 2, i) for i, m in enumerate(msgs)])
+    d_in = torch.from_numpy(cts.view(np.int64)).cuda()
+    d_lut = torch.from_numpy(luts).cuda()
+    L.lvs_ctx_set_br_split(ctx, 0)
+    outs = []
+    for staged in (False, True, False):
+        L.lvs_ctx_set_key_staging(ctx, staged)
+        assert L.lvs_ctx_key_staging(ctx) == staged
+        d_out = torch.zeros_like(d_in)
+        L.lvs_pbs_batch_device(ctx, d_in, big + 1, d_lut, d_out, big + 1, count)
+        L.lvs_ctx_synchronize(ctx)
+        outs.append(d_out.cpu().numpy().view(np.uint64).copy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    sample = list(range(count)) if which == "test" else [0, 1, 151, 152, 169]
+    want = T.pbs_many(K, cts[sample], luts[sample].astype(np.uint32))
+    assert np.array_equal(outs[1][sample], want)
+    L.lvs_ctx_free(ctx)
+
+
+def test_key_staging_wait_runs_out_reports_timeout_and_recovers():
+    """A staging copy that is never issued (test hook): the bounded wait for it
+    gives up after about a second, the launch ends normally with its results
+    void, the next synchronize returns LVS_ERR_TIMEOUT, and the same context
+    then computes bit-exact results again."""
+    params = L.lvs_params_test()
+    ck, sk = L.lvs_keygen(params, 9)
+    ctx = L.lvs_ctx_create(sk, 0)
+    K = T.Keys(T.params_test(), 9)
+    big = K.big_dim
+    count = 200
+    msgs = np.arange(count) % 32
+    luts = np.tile(np.arange(16, dtype=np.uint8), (count, 1))
+    cts = np.stack([T.encrypt(K, int(m), 23, 0, i) for i, m in enumerate(msgs)])
+    d_in = torch.from_numpy(cts.view(np.int64)).cuda()
+    d_lut = torch.from_numpy(luts).cuda()
+    L.lvs_ctx_set_br_split(ctx, 0)
+    ref = torch.zeros_like(d_in)
+    L.lvs_pbs_batch_device(ctx, d_in, big + 1, d_lut, ref, big + 1, count)
+    L.lvs_ctx_synchronize(ctx)
+    L.lvs_ctx_set_key_staging(ctx, True)
+    L.lvs_debug_drop_key_copy(ctx, True)
+    d_out = torch.zeros_like(d_in)
+    L.lvs_pbs_batch_device(ctx, d_in, big + 1, d_lut, d_out, big + 1, count)
+    with pytest.raises(L.LvsError) as e:
+        L.lvs_ctx_synchronize(ctx)
+    assert e.value.status == L.LVS_ERR_TIMEOUT
+    L.lvs_debug_drop_key_copy(ctx, False)
+    L.lvs_ctx_synchronize(ctx)   # the give-up was reported once
+    d_out.zero_()
+    L.lvs_pbs_batch_device(ctx, d_in, big + 1, d_lut, d_out, big + 1, count)
+    L.lvs_ctx_synchronize(ctx)
+    assert np.array_equal(d_out.cpu().numpy(), ref.cpu().numpy())
+    L.lvs_ctx_free(ctx)
