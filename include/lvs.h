@@ -137,6 +137,10 @@ lvs_status lvs_client_key_import(const lvs_params *params, const uint64_t *lwe_k
  * lvs_ctx_synchronize) run one at a time in the order the lock is taken. */
 lvs_status lvs_ctx_create(const lvs_server_key *sk, int device, void *stream, lvs_ctx **out);
 void lvs_ctx_free(lvs_ctx *ctx);
+/* Waits for the context's stream.  LVS_ERR_TIMEOUT if a bounded device-side
+ * wait of a kernel on this device gave up since the last check (the results of
+ * that work are void; reported once, the context stays usable); lvs_decrypt,
+ * lvs_decrypt_all, lvs_result_export and the server's steps report it too. */
 lvs_status lvs_ctx_synchronize(lvs_ctx *ctx);
 
 /* ---------------------------------------------------------------- client */
