@@ -57,3 +57,16 @@ def test_roofline_work_count():
         per_cmux_prime = ((k + 1) * l + (k + 1)) * per_transform + (k + 1) ** 2 * l * N
         assert bench.modmul_per_pbs(p) == n * 3 * per_cmux_prime
     assert bench.modmul_per_pbs(T.params_lvs()) == 210_087_936                 # 834 x 3 x 83,968
+
+
+def test_key_row_bytes():
+    """Bytes of one NTT-domain bootstrapping-key row, the unit of the key
+    product's L2 reads: 3 primes x (k+1)^2 l polynomials x N residues of 4
+    bytes; n rows make the whole device key (164 MB at the default set)."""
+    import bench
+    from oracle import tfhe as T
+    p = T.params_lvs()
+    assert bench.key_row_bytes(p) == 3 * 2 * 2 * 2 * 2048 * 4 == 196_608
+    assert p.n * bench.key_row_bytes(p) == 163_971_072
+    q = T.params_test()
+    assert bench.key_row_bytes(q) == 3 * (q.k + 1) ** 2 * q.pbs_level * q.N * 4
